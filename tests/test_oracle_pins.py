@@ -1,0 +1,371 @@
+"""Pins for the FP64 oracle against facts fixed by the paper and by mathematics, not by itself.
+
+* hand-derived worked examples (tests/golden/worked_examples.json; Eq. 1, Eq. 2, Algorithm 1);
+* closed forms on straight fibers, a library special case (point fibers reduce Eq. 2 to the
+  Euclidean distance, checked against scipy's cdist);
+* invariants of Eq. 2: d(a,a) = 0, symmetry, reversal symmetry, triangle inequality, invariance
+  under a shared rigid motion;
+* labelling against an independent brute force written as a sort over all candidates;
+* the progressive-discarding cascade (Section 2.3) against the plain definition;
+* the gradient against closed forms and central finite differences.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def _rand_fibers(rng, n, scale=30.0):
+    base = rng.normal(0, scale, size=(n, 1, 3))
+    walk = np.cumsum(rng.normal(0, 2.0, size=(n, 21, 3)), axis=1)
+    return (base + walk).astype(np.float32)
+
+
+def _rev(x):
+    return x[..., ::-1, :]
+
+
+@pytest.fixture(scope="module")
+def gold():
+    with open(GOLD) as fh:
+        return json.load(fh)
+
+
+def test_worked_examples_dme(gold):
+    for case in gold["dme_cases"]:
+        a = np.array(case["a"], np.float32)[None]
+        b = np.array(case["b"], np.float32)[None]
+        dme, dd, dr = oracle.dme_matrix(a, b)
+        assert dd[0, 0] == pytest.approx(case["dd"], abs=1e-12), case["name"]
+        assert dr[0, 0] == pytest.approx(case["dr"], abs=1e-12), case["name"]
+        assert dme[0, 0] == pytest.approx(case["dme"], abs=1e-12), case["name"]
+
+
+def test_worked_examples_labels(gold):
+    fib = np.array(gold["fiber"], np.float32)[None]
+    for case in gold["label_cases"]:
+        cen = np.array(case["centroids"], np.float32)
+        for mode in ("brute", "cascade"):
+            r = oracle.label(fib, cen, case["bundle_of"], case["thresholds"], mode)
+            assert r["labels"][0] == case["label"], (case["name"], mode)
+            assert r["cidx"][0] == case["cidx"], (case["name"], mode)
+            if case["dist"] is None:
+                assert math.isinf(r["dist"][0])
+            else:
+                assert r["dist"][0] == pytest.approx(case["dist"], abs=1e-12)
+
+
+def test_parallel_offsets_closed_form():
+    """Straight fiber vs the same fiber shifted by delta: d_ME = |delta| whenever the fiber is
+    long enough that the reversed orientation is worse (Eq. 2). Covers each coordinate and
+    both signs, so a dropped term or a sign slip shows up."""
+    rng = np.random.default_rng(7)
+    t = np.arange(21)[:, None]
+    for _ in range(50):
+        d = rng.normal(0, 3, size=3)
+        direction = rng.normal(size=3)
+        direction /= np.linalg.norm(direction)
+        a = (t * 2.0 * direction + rng.normal(0, 20, size=3)).astype(np.float64)
+        b = a + d
+        dme, dd, dr = oracle.dme_matrix(a[None].astype(np.float32), b[None].astype(np.float32))
+        a32, b32 = a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+        exact = np.linalg.norm(b32 - a32, axis=1).max()  # float32 rounding of the inputs
+        assert dd[0, 0] == pytest.approx(exact, rel=1e-12)
+        assert dd[0, 0] == pytest.approx(np.linalg.norm(d), abs=1e-4)
+        assert dme[0, 0] == dd[0, 0]
+
+
+def test_point_fibers_reduce_to_euclidean():
+    """If every point of a and of b is the same point, Eq. 2 is the Euclidean distance."""
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(3)
+    p = rng.uniform(-80, 80, size=(13, 3)).astype(np.float32)
+    q = rng.uniform(-80, 80, size=(9, 3)).astype(np.float32)
+    A = np.repeat(p[:, None, :], 21, axis=1)
+    B = np.repeat(q[:, None, :], 21, axis=1)
+    dme, dd, dr = oracle.dme_matrix(A, B)
+    ref = cdist(p.astype(np.float64), q.astype(np.float64))
+    np.testing.assert_allclose(dme, ref, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(dd, ref, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(dr, ref, rtol=1e-15, atol=0)
+
+
+def test_single_point_changes_each_coordinate():
+    """Moving one point of b by a known vector changes only that point distance; checks every
+    point index in both orientations (a wrong reversal index fails here)."""
+    a = np.zeros((21, 3), np.float32)
+    a[:, 0] = np.arange(21) * 0.01  # nearly a point: reversal distances stay below 0.2
+    for i in range(21):
+        for axis in range(3):
+            b = a.copy()
+            b[i, axis] += 7.0
+            dme, dd, dr = oracle.dme_matrix(a[None], b[None])
+            assert dd[0, 0] == pytest.approx(7.0, abs=1e-5)
+            # reversed: point j pairs with b[20-j]; the moved point pairs with a[20-i]
+            mv = b[i].astype(np.float64) - a[20 - i].astype(np.float64)
+            assert dr[0, 0] == pytest.approx(np.linalg.norm(mv), abs=1e-5)
+
+
+def test_identities():
+    rng = np.random.default_rng(11)
+    A = _rand_fibers(rng, 40)
+    B = _rand_fibers(rng, 30)
+    dAA, _, _ = oracle.dme_matrix(A, A)
+    assert np.all(np.diag(dAA) == 0.0)
+    dAB, ddAB, drAB = oracle.dme_matrix(A, B)
+    dBA, ddBA, drBA = oracle.dme_matrix(B, A)
+    np.testing.assert_array_equal(dAB, dBA.T)
+    np.testing.assert_array_equal(ddAB, ddBA.T)
+    # reversal: d(a, flip b) swaps the two orientation maxima; d(flip a, flip b) = d(a, b)
+    dAfB, ddAfB, drAfB = oracle.dme_matrix(A, _rev(B).copy())
+    np.testing.assert_array_equal(ddAfB, drAB)
+    np.testing.assert_array_equal(drAfB, ddAB)
+    dfAfB, _, _ = oracle.dme_matrix(_rev(A).copy(), _rev(B).copy())
+    np.testing.assert_array_equal(dfAfB, dAB)
+    # d(a, flip a) = 0
+    dAfA, _, _ = oracle.dme_matrix(A, _rev(A).copy())
+    assert np.all(np.diag(dAfA) == 0.0)
+
+
+def test_triangle_inequality():
+    rng = np.random.default_rng(5)
+    X = _rand_fibers(rng, 25, scale=5.0)
+    D, _, _ = oracle.dme_matrix(X, X)
+    viol = D[:, None, :] - (D[:, :, None] + D[None, :, :])
+    assert viol.max() <= 1e-9
+
+
+def test_rigid_invariance():
+    rng = np.random.default_rng(9)
+    A = _rand_fibers(rng, 20).astype(np.float64)
+    B = _rand_fibers(rng, 15).astype(np.float64)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                  [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                  [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+    t = rng.normal(0, 10, size=3)
+    D0, _, _ = oracle.dme_matrix(A.astype(np.float32), B.astype(np.float32))
+    D1, _, _ = oracle.dme_matrix((A @ R.T + t).astype(np.float32), (B @ R.T + t).astype(np.float32))
+    np.testing.assert_allclose(D1, D0, atol=2e-4)  # float32 rounding of the moved inputs
+
+
+def _brute_by_sort(fib, cen, bundle_of, thr):
+    """Independent labelling: list every (d_ME, bundle, centroid) candidate, drop the ones above
+    their threshold, take the first in (distance, bundle, centroid) order."""
+    fib = fib.astype(np.float64)
+    cen = cen.astype(np.float64)
+    out = []
+    for f in range(fib.shape[0]):
+        cands = []
+        for c in range(cen.shape[0]):
+            direct = np.sqrt(((fib[f] - cen[c]) ** 2).sum(axis=1)).max()
+            flipped = np.sqrt(((fib[f] - cen[c][::-1]) ** 2).sum(axis=1)).max()
+            d = min(direct, flipped)
+            if d <= float(np.float32(thr[bundle_of[c]])):
+                cands.append((d, int(bundle_of[c]), c))
+        if cands:
+            d, b, c = min(cands)
+            out.append((b, d, c))
+        else:
+            out.append((-1, math.inf, -1))
+    return out
+
+
+def test_labels_vs_sorted_brute_force():
+    rng = np.random.default_rng(21)
+    cen = _rand_fibers(rng, 30, scale=6.0)
+    bundle_of = rng.integers(0, 7, size=30).astype(np.int32)
+    thr = rng.uniform(3, 9, size=7).astype(np.float32)
+    fib = (cen[rng.integers(0, 30, size=60)] + rng.normal(0, 1.2, size=(60, 21, 3))).astype(
+        np.float32)
+    fib[::3] = fib[::3, ::-1]
+    ref = _brute_by_sort(fib, cen, bundle_of, thr)
+    for mode in ("brute", "cascade"):
+        r = oracle.label(fib, cen, bundle_of, thr, mode)
+        for f, (b, d, c) in enumerate(ref):
+            assert r["labels"][f] == b
+            assert r["cidx"][f] == c
+            if b >= 0:
+                assert r["dist"][f] == pytest.approx(d, rel=1e-15)
+    assert sum(1 for x in ref if x[0] >= 0) > 10
+
+
+def test_exact_ties_and_threshold_edges():
+    """Distances landing exactly on thresholds and on each other (integer offsets)."""
+    t = np.arange(21, dtype=np.float32)
+    base = np.stack([t, 0 * t, 0 * t], axis=1)
+    offs = [(0, 3, 4), (0, 0, 5), (0, 4, 3), (0, 0, 6), (0, 0, 2), (0, 2, 0)]
+    cen = np.stack([base + np.array(o, np.float32) for o in offs] +
+                   [base[::-1] + np.array(o, np.float32) for o in offs])  # reversed copies
+    bundle_of = np.array([2, 1, 1, 0, 3, 3, 4, 5, 5, 6, 7, 7], np.int32)
+    for thr in ([6.0, 5.0, 5.0, 1.9, 9, 9, 9, 9], [6.0, 5.0, 4.9, 2.0, 9, 9, 9, 9],
+                [4.0, 4.0, 4.0, 4.0, 4.0, 4.0, 4.0, 4.0], [1, 1, 1, 1, 5.0, 5.0, 6.0, 1.9],
+                [1, 1, 1, 1, 4.9, 5.0, 5.9, 2.0]):
+        thr = np.array(thr, np.float32)
+        ref = _brute_by_sort(base[None], cen, bundle_of, thr)
+        for mode in ("brute", "cascade"):
+            r = oracle.label(base[None], cen, bundle_of, thr, mode)
+            assert (r["labels"][0], r["cidx"][0]) == (ref[0][0], ref[0][2])
+
+
+def test_cascade_equals_brute_on_small_workload(small_workload):
+    atlas, fib = small_workload
+    rb = oracle.label(fib, atlas.centroids, atlas.bundle_of, atlas.thresholds, "brute")
+    rc = oracle.label(fib, atlas.centroids, atlas.bundle_of, atlas.thresholds, "cascade")
+    for k in ("labels", "dist", "cidx", "orient", "argmax"):
+        np.testing.assert_array_equal(rb[k], rc[k])
+    frac = (rb["labels"] >= 0).mean()
+    assert 0.5 < frac < 0.95
+    counts = rc["counts"]
+    assert counts[4] == fib.shape[0] * atlas.M  # every pair reaches test1
+    assert counts[0] == counts[4]  # one point distance per pair in test1
+    assert counts[5] <= counts[4] and counts[6] <= counts[5] and counts[7] <= counts[6]
+
+
+def test_nonfinite_fiber():
+    rng = np.random.default_rng(1)
+    cen = _rand_fibers(rng, 5)
+    fib = cen[:3].copy()
+    fib[1, 4, 2] = np.nan
+    fib[2, 0, 0] = np.inf
+    for mode in ("brute", "cascade"):
+        r = oracle.label(fib, cen, np.zeros(5, np.int32), np.array([100.0], np.float32), mode)
+        assert r["labels"][0] == 0 and r["dist"][0] == 0.0
+        assert list(r["labels"][1:]) == [-1, -1]
+        assert np.isnan(r["dist"][1:]).all()
+
+
+def test_near_tie_flags():
+    t = np.arange(21, dtype=np.float32)
+    base = np.stack([t, 0 * t, 0 * t], axis=1)
+    cen = np.stack([base + np.array(o, np.float32) for o in [(0, 0, 3), (0, 3.001, 0),
+                                                               (0, 0, 20)]])
+    bo = np.array([0, 1, 2], np.int32)
+    fib = np.stack([base, base + np.array([0, 0, 18.0], np.float32),
+                    base + np.array([0, 0, 8.0], np.float32)])
+    thr = np.array([5.0, 5.0, 5.0], np.float32)
+    r = oracle.label(fib, cen, bo, thr)
+    flag = oracle.near_tie(fib, cen, bo, thr, r["labels"], r["dist"])
+    # fiber 0: bundles 0 and 1 at 3 and 3.001 -> runner-up within 2e-3; fiber 1: bundle 2 at
+    # 2; fiber 2: bundle 0 at 5 exactly = its threshold -> near threshold
+    assert list(flag) == [1, 0, 1]
+    thr2 = np.array([5.0, 5.0, 2.5], np.float32)
+    r2 = oracle.label(fib, cen, bo, thr2)
+    assert list(oracle.near_tie(fib, cen, bo, thr2, r2["labels"], r2["dist"])) == [1, 0, 1]
+
+
+def test_grad_translation_closed_form():
+    """One fiber, one centroid, translation only: dC/dt = u = r/|r| at the argmax point."""
+    t = np.arange(21, dtype=np.float32)
+    fib = np.stack([t, 0 * t, 0 * t], axis=1)[None]
+    cen = fib.copy()
+    cen[0, 13] += np.array([1.0, -2.0, 2.0], np.float32)  # argmax point 13, |r| = 3
+    aff = np.array([1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0], np.float64)
+    g = oracle.grad(fib, aff, cen, [0], [10.0])
+    assert g["cost"] == pytest.approx(3.0, abs=1e-12)
+    u = -np.array([1.0, -2.0, 2.0]) / 3.0
+    np.testing.assert_allclose(g["grad_affine"][9:], u, atol=1e-15)
+    np.testing.assert_allclose(g["grad_affine"][:9].reshape(3, 3), np.outer(u, fib[0, 13]),
+                               atol=1e-12)
+    gc = np.zeros((1, 21, 3))
+    gc[0, 13] = -u
+    np.testing.assert_allclose(g["grad_centroids"], gc, atol=1e-15)
+    assert g["argmax"][0] == 13 and g["orient"][0] == 0
+
+
+def test_grad_reversed_orientation_closed_form():
+    """Same as above with the centroid stored in reversed point order: the argmax fiber point
+    13 pairs with centroid point 20 - 13 = 7 (Eq. 2 reversal), which takes the gradient."""
+    t = np.arange(21, dtype=np.float32)
+    fib = np.stack([t, 0 * t, 0 * t], axis=1)[None]
+    cen = fib[:, ::-1].copy()
+    cen[0, 7] += np.array([2.0, 1.0, -2.0], np.float32)
+    aff = np.array([1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0], np.float64)
+    g = oracle.grad(fib, aff, cen, [0], [10.0])
+    assert g["orient"][0] == 1 and g["argmax"][0] == 13
+    assert g["cost"] == pytest.approx(3.0, abs=1e-12)
+    u = -np.array([2.0, 1.0, -2.0]) / 3.0
+    np.testing.assert_allclose(g["grad_affine"][9:], u, atol=1e-15)
+    gc = np.zeros((1, 21, 3))
+    gc[0, 7] = -u
+    np.testing.assert_allclose(g["grad_centroids"], gc, atol=1e-15)
+
+
+def _stable_case(seed=4, n=60, m=25):
+    rng = np.random.default_rng(seed)
+    cen = _rand_fibers(rng, m, scale=8.0)
+    fib = (cen[rng.integers(0, m, size=n)] + rng.normal(0, 1.0, size=(n, 21, 3))).astype(
+        np.float32)
+    fib[::2] = fib[::2, ::-1]
+    bo = (np.arange(m) % 5).astype(np.int32)
+    thr = np.full(5, 6.0, np.float32)
+    return fib, cen, bo, thr
+
+
+def test_grad_frozen_structure_fd():
+    """Central differences (h = 1e-3, Richardson-extrapolated with h/2 so the O(h^2) curvature
+    term of |r| drops out) of the frozen-structure cost match the analytic gradient for the
+    affine and the centroid coordinates."""
+    fib, cen, bo, thr = _stable_case()
+    aff = np.array([1.01, 0.02, -0.01, -0.015, 0.99, 0.03, 0.01, -0.02, 1.0, 0.5, -0.3, 0.2])
+    g = oracle.grad(fib, aff, cen, bo, thr)
+    frozen = (g["cidx"], g["orient"], g["argmax"])
+    assert (g["cidx"] >= 0).sum() > 20
+
+    def cost_aff(a):
+        return oracle.grad(fib, a, cen, bo, thr, frozen=frozen, want_cen=False)["cost"]
+
+    def richardson(f, x0, e, h):
+        d1 = (f(x0 + h * e) - f(x0 - h * e)) / (2 * h)
+        d2 = (f(x0 + 0.5 * h * e) - f(x0 - 0.5 * h * e)) / h
+        return (4 * d2 - d1) / 3
+
+    for k in range(12):
+        e = np.zeros(12)
+        e[k] = 1.0
+        fd = richardson(cost_aff, aff, e, 1e-3)
+        assert fd == pytest.approx(g["grad_affine"][k], rel=1e-6, abs=1e-6)
+    rng = np.random.default_rng(0)
+    used = np.unique(g["cidx"][g["cidx"] >= 0])
+    c64 = cen.astype(np.float64)
+
+    def cost_cen(flat):
+        # steps are powers of two, so float32 holds the moved coordinates exactly
+        return oracle.grad(fib, aff, flat.reshape(cen.shape).astype(np.float32), bo, thr,
+                           frozen=frozen, want_cen=False)["cost"]
+
+    for _ in range(12):
+        c = int(rng.choice(used))
+        p, ax = int(rng.integers(21)), int(rng.integers(3))
+        e = np.zeros(c64.size)
+        e[(c * 21 + p) * 3 + ax] = 1.0
+        fd = richardson(cost_cen, c64.reshape(-1), e, 2.0 ** -8)
+        assert fd == pytest.approx(g["grad_centroids"][c, p, ax], rel=1e-5, abs=1e-5)
+
+
+def test_grad_free_structure_fd():
+    """Central differences of the full forward (labels recomputed) agree on the affine gradient
+    when no fiber changes its structure within +-h."""
+    fib, cen, bo, thr = _stable_case(seed=8)
+    aff = np.array([1, 0, 0, 0, 1, 0, 0, 0, 1, 0.1, 0.2, -0.1], np.float64)
+    g = oracle.grad(fib, aff, cen, bo, thr)
+    h = 1e-4
+    for k in range(12):
+        e = np.zeros(12)
+        e[k] = h
+        gp = oracle.grad(fib, aff + e, cen, bo, thr, want_cen=False)
+        gm = oracle.grad(fib, aff - e, cen, bo, thr, want_cen=False)
+        same = all(np.array_equal(gp[x], g[x]) and np.array_equal(gm[x], g[x])
+                   for x in ("cidx", "orient", "argmax"))
+        if not same:
+            continue
+        fd = (gp["cost"] - gm["cost"]) / (2 * h)
+        assert fd == pytest.approx(g["grad_affine"][k], rel=1e-5, abs=1e-5)
