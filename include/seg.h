@@ -1,0 +1,181 @@
+/*
+ * seg.h - C ABI of libseg, GB300 (sm_103a) atlas-based fiber bundle segmentation.
+ *
+ * Method (arXiv:1912.11494, Section 2.3-2.4): every subject fiber, resampled to 21 points, is
+ * compared with every atlas centroid by the maximum point-pair Euclidean distance
+ *     d_ME(a, b) = min( max_i |a_i - b_i|, max_i |a_i - b_(20-i)| )          (Eq. 1, Eq. 2)
+ * and labelled with the bundle of the closest centroid whose bundle threshold it passes
+ * (d_ME <= theta), or -1 (Algorithm 1, closest-bundle classification).
+ *
+ * Conventions shared by every entry point:
+ *  - Coordinates are float32 millimetres, fibers and centroids laid out [count][21][3]
+ *    (point-major, xyz innermost), C-contiguous, 4-byte aligned.
+ *  - Pointers named d_* are device memory owned by the caller; h_* are host memory owned by
+ *    the caller. The library keeps no pointer to caller memory after a call returns, except
+ *    that asynchronous work queued on `stream` reads and writes it until the stream reaches it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Unless a
+ *    function says otherwise it only enqueues work on `stream` and returns without waiting.
+ *  - Argument errors are detected synchronously and returned before anything is enqueued.
+ *    Errors found on the device (a bounded wait that timed out, a full survivor list that could
+ *    not be recovered) are recorded in the atlas's device status word; seg_sync_status() waits
+ *    for the stream and reports them. No C++ exception crosses this boundary.
+ *  - Labels are bundle indices in the caller's numbering; centroid indices (cidx) are positions
+ *    in the caller's centroid array.
+ *  - Tie rule (Algorithm 1 visits bundles in increasing index, the centroids of a bundle in
+ *    their given order, and replaces the best only on a strict decrease): among centroids at the
+ *    same float32 squared distance the lowest bundle wins, then the lowest centroid index.
+ *  - A fiber with any non-finite coordinate gets label -1 and distance NaN.
+ *  - Every entry point is safe to call from several host threads; calls on one atlas from
+ *    different streams may overlap, because per-call scratch is stream-ordered.
+ */
+#ifndef SEG_H_
+#define SEG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEG_NPTS 21 /* points per fiber and per centroid (Section 2.2, 2.3) */
+
+typedef enum {
+    SEG_OK = 0,
+    SEG_ERR_INVALID_ARG = 1, /* bad size, NULL where a buffer is required, bad bundle id ... */
+    SEG_ERR_CUDA = 2,        /* a CUDA runtime call failed; seg_last_error() has the text */
+    SEG_ERR_OOM = 3,         /* device allocation failed */
+    SEG_ERR_UNSUPPORTED = 4, /* mode or device not supported (needs sm_103a) */
+    SEG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up; results of that call invalid */
+    SEG_ERR_OVERFLOW = 6     /* a fixed-capacity device list overflowed and was not recovered */
+} seg_status;
+
+typedef enum {
+    /* Exact FP32 kernel: test1 (centre point) then test2 (end points), test3 (four
+     * intermediate points), test4 (all points), each with early exit (Section 2.3-2.4). */
+    SEG_MODE_PLAIN = 0,
+    /* Tensor-core prune, then the exact test on survivors. The prune is a conservative lower
+     * bound d_ME^2 >= (|A|^2 + |B|^2 - 2 A.B) / 21 over the 63 coordinates, for the direct and
+     * the reversed centroid, from a BF16 (or TF32) GEMM with FP32 accumulation and a rounding
+     * margin. Labels and distances equal SEG_MODE_PLAIN's. Not in the paper. */
+    SEG_MODE_GEMM_BF16 = 1,
+    SEG_MODE_GEMM_TF32 = 2
+} seg_mode;
+
+typedef struct seg_atlas seg_atlas; /* opaque; owns its device copies of the atlas */
+
+/* Human-readable name of a status code (static string). */
+const char* seg_status_string(seg_status s);
+
+/* Text of the last error raised by a seg_* call on this host thread ("" if none). */
+const char* seg_last_error(void);
+
+/*
+ * Build an atlas handle (the atlasData of Algorithm 1; 21-point centroids grouped in bundles,
+ * Section 2.2; per-bundle thresholds, Section 2.3).
+ *   d_centroids  device float32 [M][21][3], finite.
+ *   d_bundle_of  device int32 [M], values in [0, B).
+ *   d_thresholds device float32 [B], finite and > 0, millimetres.
+ *   M >= 1, B >= 1, npts must equal SEG_NPTS.
+ *   out          receives the handle; release it with seg_destroy_atlas().
+ * The handle holds sorted bundle-major copies of the centroids and the operands of the tensor-
+ * core prune (about 0.9 KB per centroid). This call copies the bundle ids and thresholds to
+ * the host to validate them and SYNCHRONIZES `stream` before returning.
+ */
+seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of,
+                            const float* d_thresholds, int32_t M, int32_t B, int32_t npts,
+                            void* stream, seg_atlas** out);
+
+/* Release a handle (NULL is accepted). Waits for the device to finish using it. */
+seg_status seg_destroy_atlas(seg_atlas* atlas);
+
+/* Number of centroids M and bundles B of a handle. */
+seg_status seg_atlas_info(const seg_atlas* atlas, int32_t* M, int32_t* B);
+
+/*
+ * Label n fibers (Algorithm 1 with progressive discarding, Section 2.3; closest bundle only,
+ * Section 2.4).
+ *   d_fibers  device float32 [n][21][3]; n >= 0 (n = 0 does nothing).
+ *   mode      a seg_mode.
+ *   d_labels  device int32 [n]: bundle index, or -1 if no centroid passes (required).
+ *   d_dist    device float32 [n] or NULL: d_ME to the chosen centroid, +inf if none.
+ *   d_cidx    device int32 [n] or NULL: chosen centroid (caller's index), -1 if none.
+ *   d_orient  device uint8 [n] or NULL: 0 direct, 1 reversed (ties go to direct).
+ * Output buffers must not overlap the input. Scratch (GEMM modes) is allocated stream-ordered
+ * on `stream` and released before the call's work completes.
+ */
+seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, seg_mode mode,
+                     int32_t* d_labels, float* d_dist, int32_t* d_cidx, uint8_t* d_orient,
+                     void* stream);
+
+/*
+ * Label nsubj subjects of uneven size in one persistent launch (not in the paper; the paper
+ * labels one subject at a time, Section 3). Subject s has h_counts[s] >= 0 fibers at device
+ * pointer h_fibers[s] and writes h_labels[s] (required) and h_dist[s] (array or entries may be
+ * NULL). The pointer arrays are host memory read during the call. Results per subject equal
+ * seg_label's. The launch sequence is captured once into a CUDA graph per (atlas, nsubj) and
+ * replayed with a new work table; the first call per shape pays the capture.
+ */
+seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,
+                           const int64_t* h_counts, seg_mode mode, int32_t* const* h_labels,
+                           float* const* h_dist, void* stream);
+
+/*
+ * y = A x + t for every point of n fibers (float32 in and out, FP32 arithmetic).
+ * h_affine12: host float64 [12], A row-major (9) then t (3). d_out may equal d_in.
+ * Not in the paper: the affine is the subject-to-atlas registration refined through seg_grad.
+ */
+seg_status seg_apply_affine(const float* d_in, int64_t n, const double* h_affine12, float* d_out,
+                            void* stream);
+
+/*
+ * Gradient of C = sum over labelled fibers of d_ME(T f, c_sigma(f)), T f = A f + t applied to
+ * every point, through the argmax point (subgradient; not in the paper).
+ *   d_fibers        device float32 [n][21][3], the UNtransformed fibers.
+ *   h_affine12      host float64 [12], the affine at which the forward ran.
+ *   d_cidx, d_orient the forward's outputs for the transformed fibers (seg_label on
+ *                   seg_apply_affine's result): chosen centroid (caller index, -1 = none) and
+ *                   orientation.
+ *   d_grad_affine12 device float64 [12] (required): dC/dA row-major, then dC/dt. Per-fiber
+ *                   terms are FP32; the sum over fibers is FP64 with a fixed order, so the
+ *                   result is deterministic.
+ *   d_grad_centroids device float32 [M][21][3] or NULL: dC/dc (overwritten, not accumulated).
+ *   d_cost          device float64 [1] or NULL: C.
+ * The argmax point is recomputed from the fiber and centroid: the lowest point index attaining
+ * the maximum point distance in the saved orientation. A zero distance contributes zero.
+ */
+seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                    const double* h_affine12, const int32_t* d_cidx, const uint8_t* d_orient,
+                    double* d_grad_affine12, float* d_grad_centroids, double* d_cost,
+                    void* stream);
+
+/*
+ * Tile shapes of a mode's kernels (the autotuner's search space; not in the paper).
+ * seg_num_configs returns how many shapes `mode` has (>= 1). seg_set_config selects shape
+ * `config` in [0, seg_num_configs(mode)) for later calls on this atlas; 0 is the default. Every
+ * shape gives identical results; only speed differs. seg_get_config reads the selection.
+ */
+int32_t seg_num_configs(seg_mode mode);
+seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config);
+seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config);
+
+/*
+ * Wait for `stream`, then report and clear the atlas's device status word: SEG_OK, or the first
+ * device-side error (SEG_ERR_TIMEOUT, SEG_ERR_OVERFLOW) recorded since the last call.
+ */
+seg_status seg_sync_status(const seg_atlas* atlas, void* stream);
+
+/*
+ * Statistics of the last GEMM-mode seg_label on this atlas (read after the stream finished):
+ * pairs = fibers x 2M (fiber, centroid, orientation) candidates screened, survivors = those
+ * kept by the tensor-core bound, overflow_fibers = fibers rescanned by the exact kernel because
+ * the survivor list was full. Any pointer may be NULL.
+ */
+seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
+                          int64_t* overflow_fibers);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEG_H_ */

@@ -1,0 +1,279 @@
+// SEG_MODE_PLAIN: exact FP32 labelling (Algorithm 1 with the progressive discarding of
+// Section 2.3, closest bundle of Section 2.4).
+//
+// Work split: every warp owns a tile of TW = 32 consecutive fibers for the whole atlas and runs
+// independently of the other warps of its CTA (no CTA barrier anywhere), so no fiber result
+// crosses warps and the latency of one warp's exact checks is hidden by the others. The warp's
+// tile (32 x 252 B) is copied into its slice of shared memory by the TMA engine (1D bulk copy).
+// The atlas is walked in chunks of 32*C centroids, sorted bundle-major; each lane keeps C
+// centroids of the chunk in registers (the next chunk is prefetched while the current one is
+// screened) and the fibers of the tile are broadcast from shared memory.
+//
+// test1 (Section 2.3: the centre point, shared by both orientations) is evaluated in dot-product
+// form, |a-b|^2 <= theta^2  <=>  a.b + (theta^2 - |b|^2)/2 >= |a|^2/2, i.e. three FMAs and one
+// compare per pair, with a rounding slack that only ever keeps more pairs (the slack covers the
+// FP32 error of the dot form, so no pair the exact test would accept is dropped). The warp only
+// looks at which pairs passed when its vote over a block of K fibers says one did; passing pairs
+// are appended to the warp's queue and drained 32 at a time, one pair per lane, through the
+// exact FP32 cascade (test1..test4 on squared distances, bound min(theta^2, best^2)). The result
+// is merged into the fiber's packed key (d^2 bits, sorted centroid index, orientation) with a
+// shared-memory atomicMin. The key order is (distance, bundle-major centroid index), i.e.
+// Algorithm 1's strict-decrease update over its visiting order.
+#include <math.h>
+
+#include "seg_exact.cuh"
+#include "seg_internal.cuh"
+#include "seg_ptx.cuh"
+
+namespace seg {
+namespace {
+
+constexpr int PW = 4;    // independent warps per CTA
+constexpr int TW = 32;   // fibers per warp tile
+
+template <int PC, int PK>
+struct WarpSmem {
+    static constexpr int QW = 32 + PK * PC * 32;  // queue: one drain batch + one block's worth
+    static constexpr size_t fc_off = 0;                        // [TW][63] floats
+    static constexpr size_t fs_off = fc_off + TW * NC * 4;     // [TW] float4
+    static constexpr size_t key_off = fs_off + TW * 16;        // [TW] u64
+    static constexpr size_t q_off = key_off + TW * 8;          // [QW] u32
+    static constexpr size_t bar_off = (q_off + QW * 4 + 15) / 16 * 16;
+    static constexpr size_t bytes = bar_off + 16;
+};
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// max over C values with 3-input max
+template <int C>
+__device__ __forceinline__ float maxn(const float* t) {
+    if constexpr (C == 1) {
+        return t[0];
+    } else if constexpr (C == 2) {
+        return fmaxf(t[0], t[1]);
+    } else {
+        float m = fmax3(t[0], t[1], t[2]);
+#pragma unroll
+        for (int c = 3; c + 1 < C; c += 2) m = fmax3(m, t[c], t[c + 1]);
+        if constexpr (C % 2 == 0) m = fmaxf(m, t[C - 1]);
+        return m;
+    }
+}
+
+__device__ __forceinline__ float key_best2(unsigned long long k) {
+    return __uint_as_float((unsigned)(k >> 32));  // NaN for the empty key: fminf ignores it
+}
+
+// Exact check of one queued pair e = (sorted centroid << 8 | tile fiber); merges into the
+// fiber's key.
+__device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float* fc,
+                                                unsigned long long* key, unsigned e) {
+    const int c = (int)(e >> 8);
+    const int f = (int)(e & 255u);
+    const float bound = fminf(__ldg(at.thr2 + c), key_best2(key[f]));
+    float d2;
+    int o;
+    if (exact_pair(fc + f * NC, at.cen + (size_t)c * CROW, bound, d2, o)) {
+        const unsigned long long k = ((unsigned long long)__float_as_uint(d2) << 32) |
+                                     ((unsigned long long)c << 1) | (unsigned)o;
+        atomicMin(key + f, k);
+    }
+}
+
+template <int PC, int PK>
+__global__ void __launch_bounds__(PW * 32)
+k_label_plain(const float* __restrict__ fib, long long n, AtlasView at, int fib_aligned,
+              int* __restrict__ labels, float* __restrict__ dist, int* __restrict__ cidx,
+              unsigned char* __restrict__ orient) {
+    using WS = WarpSmem<PC, PK>;
+    constexpr int CH = 32 * PC;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* ws = smem + warp * WS::bytes;
+    float* fc = reinterpret_cast<float*>(ws + WS::fc_off);
+    float4* fs = reinterpret_cast<float4*>(ws + WS::fs_off);
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(ws + WS::key_off);
+    unsigned* q = reinterpret_cast<unsigned*>(ws + WS::q_off);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ws + WS::bar_off);
+
+    const long long f0 = ((long long)blockIdx.x * PW + warp) * TW;
+    if (f0 >= n) return;  // warp-uniform
+    const int nf = (int)min((long long)TW, n - f0);
+    const bool tma_tile = fib_aligned && nf == TW;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (tma_tile) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, (uint32_t)(TW * NC * 4));
+            bulk_g2s(fc, fib + f0 * NC, (uint32_t)(TW * NC * 4), bar);
+        }
+    } else {
+        for (int k = lane; k < nf * NC; k += 32) fc[k] = __ldg(fib + f0 * NC + k);
+    }
+    key[lane] = ~0ull;
+    // first centroid chunk goes to registers while the tile arrives
+    float4 nxt[PC];
+#pragma unroll
+    for (int c = 0; c < PC; ++c) nxt[c] = __ldg(at.scr2 + c * 32 + lane);
+    (void)WS::QW;
+    int ok = 1;
+    if (tma_tile && lane == 0) ok = (int)mbar_wait_bounded(bar, 0);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    if (!ok) {
+        if (lane == 0) {
+            atomicOr(at.status, ST_TIMEOUT);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+    // per-fiber screening data: centred centre point and |a|^2/2 minus its rounding slack;
+    // a fiber with a non-finite coordinate gets NaN (never passes) and is reported as such.
+    {
+        float4 v = make_float4(0.f, 0.f, 0.f, INFINITY);
+        if (lane < nf) {
+            const float* a = fc + lane * NC;
+            bool finite = true;
+            for (int k = 0; k < NC; ++k) finite = finite && isfinite(a[k]);
+            const float x = a[3 * CENTRE] - at.c0x, y = a[3 * CENTRE + 1] - at.c0y,
+                        z = a[3 * CENTRE + 2] - at.c0z;
+            const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+            v = make_float4(x, y, z, finite ? 0.5f * r2 - 1e-5f * r2 - 1e-3f : NAN);
+        }
+        fs[lane] = v;
+    }
+    __syncwarp();
+
+    const unsigned lt = (1u << lane) - 1u;
+    const int nch = at.M_pad / CH;
+    const int nfk = (nf + PK - 1) / PK * PK;
+    int qn = 0;
+    for (int j = 0; j < nch; ++j) {
+        float bx[PC], by[PC], bz[PC], mg[PC];
+#pragma unroll
+        for (int c = 0; c < PC; ++c) {
+            bx[c] = nxt[c].x;
+            by[c] = nxt[c].y;
+            bz[c] = nxt[c].z;
+            mg[c] = nxt[c].w;
+        }
+        if (j + 1 < nch) {
+#pragma unroll
+            for (int c = 0; c < PC; ++c) nxt[c] = __ldg(at.scr2 + (size_t)(j + 1) * CH + c * 32 + lane);
+        }
+        const unsigned cbase = (unsigned)(j * CH + lane);
+        for (int f = 0; f < nfk; f += PK) {
+            // score_k = max_c (a_k.b_c + mg_c) - h_k >= 0  <=>  some centroid passes test1
+            float sk[PK];
+#pragma unroll
+            for (int k = 0; k < PK; ++k) {
+                const float4 a = fs[f + k];
+                float t[PC];
+#pragma unroll
+                for (int c = 0; c < PC; ++c)
+                    t[c] = fmaf(a.z, bz[c], fmaf(a.y, by[c], fmaf(a.x, bx[c], mg[c])));
+                sk[k] = maxn<PC>(t) - a.w;
+            }
+            if (__any_sync(0xffffffffu, maxn<PK>(sk) >= 0.0f)) {
+#pragma unroll
+                for (int k = 0; k < PK; ++k) {
+                    if (__any_sync(0xffffffffu, sk[k] >= 0.0f)) {
+                        const float4 a = fs[f + k];
+#pragma unroll
+                        for (int c = 0; c < PC; ++c) {
+                            const float t =
+                                fmaf(a.z, bz[c], fmaf(a.y, by[c], fmaf(a.x, bx[c], mg[c])));
+                            const bool p = t >= a.w;
+                            const unsigned m = __ballot_sync(0xffffffffu, p);
+                            if (p)
+                                q[qn + __popc(m & lt)] =
+                                    ((cbase + (unsigned)(c * 32)) << 8) | (unsigned)(f + k);
+                            qn += __popc(m);
+                        }
+                    }
+                }
+                __syncwarp();
+                while (qn >= 32) {
+                    const unsigned e = q[qn - 32 + lane];
+                    __syncwarp();
+                    qn -= 32;
+                    exact_and_merge(at, fc, key, e);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) exact_and_merge(at, fc, key, q[lane]);
+    __syncwarp();
+    if (lane < nf) {
+        const long long gi = f0 + lane;
+        const unsigned long long k = key[lane];
+        if (isnan(fs[lane].w)) {
+            labels[gi] = -1;
+            if (dist) dist[gi] = NAN;
+            if (cidx) cidx[gi] = -1;
+            if (orient) orient[gi] = 0;
+        } else if (k == ~0ull) {
+            labels[gi] = -1;
+            if (dist) dist[gi] = INFINITY;
+            if (cidx) cidx[gi] = -1;
+            if (orient) orient[gi] = 0;
+        } else {
+            const int c = (int)((k & 0xffffffffull) >> 1);
+            labels[gi] = at.bundle[c];
+            if (dist) dist[gi] = sqrtf(__uint_as_float((unsigned)(k >> 32)));
+            if (cidx) cidx[gi] = at.perm[c];
+            if (orient) orient[gi] = (unsigned char)(k & 1ull);
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+template <int PC, int PK>
+cudaError_t launch_cfg(const AtlasView& at, const float* fib, long long n, int* labels,
+                       float* dist, int* cidx, unsigned char* orient, cudaStream_t st) {
+    static_assert(TW % PK == 0 && MPAD % (32 * PC) == 0, "tile shape");
+    const size_t smem = PW * WarpSmem<PC, PK>::bytes;
+    auto kern = k_label_plain<PC, PK>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    const long long tiles = (n + TW - 1) / TW;
+    const long long grid = (tiles + PW - 1) / PW;
+    const int aligned = ((uintptr_t)fib % 16) == 0;
+    kern<<<(unsigned)grid, PW * 32, smem, st>>>(fib, n, at, aligned, labels, dist, cidx, orient);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tile shapes (centroids per lane, fibers per vote) the autotuner chooses from.
+// Entry 0 is the default (fastest measured on the 4,145,000 x 10,000 workload).
+const int kPlainConfigs[][2] = {{8, 4}, {4, 2}, {4, 4}, {8, 2}, {2, 8}, {4, 8}};
+const int kNumPlainConfigs = 6;
+
+cudaError_t launch_label_plain(const AtlasView& at, const float* fib, long long n, int* labels,
+                               float* dist, int* cidx, unsigned char* orient, cudaStream_t st,
+                               int config) {
+    if (n <= 0) return cudaSuccess;
+    switch (config) {
+        case 1: return launch_cfg<4, 2>(at, fib, n, labels, dist, cidx, orient, st);
+        case 2: return launch_cfg<4, 4>(at, fib, n, labels, dist, cidx, orient, st);
+        case 3: return launch_cfg<8, 2>(at, fib, n, labels, dist, cidx, orient, st);
+        case 4: return launch_cfg<2, 8>(at, fib, n, labels, dist, cidx, orient, st);
+        case 5: return launch_cfg<4, 8>(at, fib, n, labels, dist, cidx, orient, st);
+        default: return launch_cfg<8, 4>(at, fib, n, labels, dist, cidx, orient, st);
+    }
+}
+
+}  // namespace seg

@@ -1,0 +1,380 @@
+// C ABI entry points of libseg (declared in include/seg.h): argument checks, the atlas handle
+// and its preparation kernel, dispatch to the labelling kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "seg_internal.cuh"
+
+namespace seg {
+
+thread_local std::string g_last_error;
+
+seg_status fail(seg_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+seg_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? SEG_ERR_OOM : SEG_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+namespace {
+
+// Sorted copy of the atlas: row s of the output is caller centroid perm[s].
+__global__ void k_prep_atlas(const float* __restrict__ cen, const int* __restrict__ bundle_of,
+                             const float* __restrict__ thr, const int* __restrict__ perm, int M,
+                             int M_pad, float c0x, float c0y, float c0z, float* __restrict__ cs,
+                             float4* __restrict__ scr, float4* __restrict__ scr2,
+                             float* __restrict__ thr2, int* __restrict__ bundle) {
+    const int s = blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= M_pad) return;
+    if (s >= M) {
+        if (threadIdx.x == 0) scr2[s] = make_float4(0.f, 0.f, 0.f, -INFINITY);
+        return;
+    }
+    const int c = perm[s];
+    const float* src = cen + (size_t)c * NC;
+    float* dst = cs + (size_t)s * CROW;
+    for (int k = threadIdx.x; k < CROW; k += blockDim.x) dst[k] = k < NC ? src[k] : 0.0f;
+    if (threadIdx.x == 0) {
+        const int b = bundle_of[c];
+        const float t = thr[b];
+        const float t2 = t * t;
+        bundle[s] = b;
+        thr2[s] = t2;
+        scr[s] = make_float4(src[3 * CENTRE], src[3 * CENTRE + 1], src[3 * CENTRE + 2], t2);
+        // test1 in dot-product form (see k_plain.cu); the slack only keeps more pairs
+        const float x = src[3 * CENTRE] - c0x, y = src[3 * CENTRE + 1] - c0y,
+                    z = src[3 * CENTRE + 2] - c0z;
+        const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+        scr2[s] = make_float4(x, y, z, 0.5f * (t2 - r2) + 1e-5f * (r2 + t2) + 1e-3f);
+    }
+}
+
+bool device_is_sm103(int* dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (dev_out) *dev_out = dev;
+    return major == 10 && minor == 3;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+}  // namespace
+}  // namespace seg
+
+using namespace seg;
+
+struct seg_atlas {
+    AtlasView view{};
+    int device = 0;
+    float* cen = nullptr;
+    float4* scr = nullptr;
+    float4* scr2 = nullptr;
+    float* thr2 = nullptr;
+    int* bundle = nullptr;
+    int* perm = nullptr;
+    int* inv_perm = nullptr;
+    unsigned* status = nullptr;
+    GemmAtlas gemm{};
+    ScratchArena scratch{};
+    BatchState batch{};
+    int config[3] = {0, 0, 0};  // tile-shape selection per seg_mode
+    std::mutex mu;  // guards scratch growth and the batch graph cache
+};
+
+extern "C" {
+
+const char* seg_status_string(seg_status s) {
+    switch (s) {
+        case SEG_OK: return "SEG_OK";
+        case SEG_ERR_INVALID_ARG: return "SEG_ERR_INVALID_ARG";
+        case SEG_ERR_CUDA: return "SEG_ERR_CUDA";
+        case SEG_ERR_OOM: return "SEG_ERR_OOM";
+        case SEG_ERR_UNSUPPORTED: return "SEG_ERR_UNSUPPORTED";
+        case SEG_ERR_TIMEOUT: return "SEG_ERR_TIMEOUT";
+        case SEG_ERR_OVERFLOW: return "SEG_ERR_OVERFLOW";
+    }
+    return "SEG_ERR_UNKNOWN";
+}
+
+const char* seg_last_error(void) { return g_last_error.c_str(); }
+
+static void free_atlas(seg_atlas* a) {
+    if (!a) return;
+    cudaFree(a->cen);
+    cudaFree(a->scr);
+    cudaFree(a->scr2);
+    cudaFree(a->thr2);
+    cudaFree(a->bundle);
+    cudaFree(a->perm);
+    cudaFree(a->inv_perm);
+    cudaFree(a->status);
+    free_gemm_atlas(&a->gemm);
+    free_scratch(&a->scratch);
+    free_batch(&a->batch);
+    delete a;
+}
+
+seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of,
+                            const float* d_thresholds, int32_t M, int32_t B, int32_t npts,
+                            void* stream, seg_atlas** out) {
+    g_last_error.clear();
+    if (!out) return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: out is NULL");
+    *out = nullptr;
+    if (!d_centroids || !d_bundle_of || !d_thresholds)
+        return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: NULL input buffer");
+    if (M < 1 || B < 1) return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: M=%d B=%d", M, B);
+    if (M > (1 << 28)) return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: M=%d too large", M);
+    if (npts != SEG_NPTS)
+        return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: npts=%d, must be %d", npts, SEG_NPTS);
+    int dev = 0;
+    if (!device_is_sm103(&dev))
+        return fail(SEG_ERR_UNSUPPORTED, "seg_create_atlas: device is not compute capability 10.3");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    std::vector<int32_t> hb(M);
+    std::vector<float> ht(B);
+    std::vector<float> hc((size_t)M * NC);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(hb.data(), d_bundle_of, M * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(ht.data(), d_thresholds, B * sizeof(float), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(hc.data(), d_centroids, hc.size() * sizeof(float), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "seg_create_atlas: reading the atlas");
+    for (int b = 0; b < B; ++b)
+        if (!(std::isfinite(ht[b]) && ht[b] > 0.0f))
+            return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: threshold[%d]=%g must be finite and > 0", b, (double)ht[b]);
+    for (size_t k = 0; k < hc.size(); ++k)
+        if (!std::isfinite(hc[k]))
+            return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: centroid %zu has a non-finite coordinate", k / NC);
+    // Stable counting sort by bundle: the visiting order of Algorithm 1.
+    std::vector<int32_t> cnt(B + 1, 0), perm(M);
+    for (int c = 0; c < M; ++c) {
+        if (hb[c] < 0 || hb[c] >= B)
+            return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: bundle_of[%d]=%d outside [0,%d)", c, hb[c], B);
+        cnt[hb[c] + 1]++;
+    }
+    for (int b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
+    for (int c = 0; c < M; ++c) perm[cnt[hb[c]]++] = c;
+    std::vector<int32_t> inv(M);
+    for (int sp = 0; sp < M; ++sp) inv[perm[sp]] = sp;
+    const int M_pad = (M + MPAD - 1) / MPAD * MPAD;
+    double c0[3] = {0.0, 0.0, 0.0};  // centring offset: mean centroid centre point
+    for (int c = 0; c < M; ++c)
+        for (int r = 0; r < 3; ++r) c0[r] += hc[(size_t)c * NC + 3 * CENTRE + r];
+    for (int r = 0; r < 3; ++r) c0[r] = std::round(c0[r] / M);
+
+    seg_atlas* a = new seg_atlas();
+    a->device = dev;
+    if ((e = dalloc(&a->cen, (size_t)M * CROW)) || (e = dalloc(&a->scr, M)) || (e = dalloc(&a->scr2, M_pad)) ||
+        (e = dalloc(&a->thr2, M)) || (e = dalloc(&a->bundle, M)) || (e = dalloc(&a->perm, M)) ||
+        (e = dalloc(&a->inv_perm, M)) || (e = dalloc(&a->status, 4))) {
+        free_atlas(a);
+        return cuda_fail(e, "seg_create_atlas: allocation");
+    }
+    if ((e = cudaMemcpyAsync(a->perm, perm.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(a->inv_perm, inv.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemsetAsync(a->status, 0, 4 * sizeof(unsigned), st))) {
+        free_atlas(a);
+        return cuda_fail(e, "seg_create_atlas: upload");
+    }
+    dim3 blk(32, 8);
+    k_prep_atlas<<<(M_pad + 7) / 8, blk, 0, st>>>(d_centroids, d_bundle_of, d_thresholds,
+                                                  a->perm, M, M_pad, (float)c0[0], (float)c0[1],
+                                                  (float)c0[2], a->cen, a->scr, a->scr2, a->thr2,
+                                                  a->bundle);
+    if ((e = cudaGetLastError())) {
+        free_atlas(a);
+        return cuda_fail(e, "seg_create_atlas: prep kernel");
+    }
+    a->view.M = M;
+    a->view.B = B;
+    a->view.M_pad = M_pad;
+    a->view.c0x = (float)c0[0];
+    a->view.c0y = (float)c0[1];
+    a->view.c0z = (float)c0[2];
+    a->view.scr2 = a->scr2;
+    a->view.cen = a->cen;
+    a->view.scr = a->scr;
+    a->view.thr2 = a->thr2;
+    a->view.bundle = a->bundle;
+    a->view.perm = a->perm;
+    a->view.status = a->status;
+    seg_status s = prep_gemm_atlas(a->view, &a->gemm, st);
+    if (s != SEG_OK) {
+        free_atlas(a);
+        return s;
+    }
+    if ((e = cudaStreamSynchronize(st))) {
+        free_atlas(a);
+        return cuda_fail(e, "seg_create_atlas: synchronize");
+    }
+    *out = a;
+    return SEG_OK;
+}
+
+seg_status seg_destroy_atlas(seg_atlas* atlas) {
+    g_last_error.clear();
+    if (!atlas) return SEG_OK;
+    cudaDeviceSynchronize();
+    free_atlas(atlas);
+    return SEG_OK;
+}
+
+seg_status seg_atlas_info(const seg_atlas* atlas, int32_t* M, int32_t* B) {
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_atlas_info: atlas is NULL");
+    if (M) *M = atlas->view.M;
+    if (B) *B = atlas->view.B;
+    return SEG_OK;
+}
+
+seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, seg_mode mode,
+                     int32_t* d_labels, float* d_dist, int32_t* d_cidx, uint8_t* d_orient,
+                     void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld < 0", (long long)n);
+    if (n > 0 && (!d_fibers || !d_labels))
+        return fail(SEG_ERR_INVALID_ARG, "seg_label: NULL fibers or labels");
+    if (mode != SEG_MODE_PLAIN && mode != SEG_MODE_GEMM_BF16 && mode != SEG_MODE_GEMM_TF32)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label: unknown mode %d", (int)mode);
+    if (n == 0) return SEG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == SEG_MODE_PLAIN) {
+        cudaError_t e = launch_label_plain(atlas->view, d_fibers, n, d_labels, d_dist, d_cidx,
+                                           d_orient, st, atlas->config[0]);
+        return e ? cuda_fail(e, "seg_label: plain kernel") : SEG_OK;
+    }
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n,
+                      mode == SEG_MODE_GEMM_TF32, d_labels, d_dist, d_cidx, d_orient, st);
+}
+
+seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,
+                           const int64_t* h_counts, seg_mode mode, int32_t* const* h_labels,
+                           float* const* h_dist, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: atlas is NULL");
+    if (nsubj < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: nsubj=%d < 0", nsubj);
+    if (nsubj == 0) return SEG_OK;
+    if (!h_fibers || !h_counts || !h_labels)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: NULL pointer array");
+    if (mode != SEG_MODE_PLAIN && mode != SEG_MODE_GEMM_BF16 && mode != SEG_MODE_GEMM_TF32)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: unknown mode %d", (int)mode);
+    for (int s = 0; s < nsubj; ++s) {
+        if (h_counts[s] < 0)
+            return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: count[%d] < 0", s);
+        if (h_counts[s] > 0 && (!h_fibers[s] || !h_labels[s]))
+            return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: NULL buffer for subject %d", s);
+    }
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    return batch_launch(a->view, &a->gemm, &a->batch, &a->scratch, &a->mu, nsubj, h_fibers,
+                        reinterpret_cast<const long long*>(h_counts), (int)mode, h_labels,
+                        h_dist, (cudaStream_t)stream);
+}
+
+seg_status seg_apply_affine(const float* d_in, int64_t n, const double* h_affine12, float* d_out,
+                            void* stream) {
+    g_last_error.clear();
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: n < 0");
+    if (!h_affine12) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: NULL affine");
+    if (n == 0) return SEG_OK;
+    if (!d_in || !d_out) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: NULL buffer");
+    return apply_affine_launch(d_in, n, h_affine12, d_out, (cudaStream_t)stream);
+}
+
+seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                    const double* h_affine12, const int32_t* d_cidx, const uint8_t* d_orient,
+                    double* d_grad_affine12, float* d_grad_centroids, double* d_cost,
+                    void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_grad: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_grad: n < 0");
+    if (!h_affine12 || !d_grad_affine12)
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad: NULL affine or gradient buffer");
+    if (n > 0 && (!d_fibers || !d_cidx || !d_orient))
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad: NULL fibers, cidx or orient");
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    return grad_launch(a->view, a->inv_perm, &a->scratch, &a->mu, d_fibers, n, h_affine12,
+                       d_cidx, d_orient, d_grad_affine12, d_grad_centroids, d_cost,
+                       (cudaStream_t)stream);
+}
+
+int32_t seg_num_configs(seg_mode mode) {
+    switch (mode) {
+        case SEG_MODE_PLAIN: return kNumPlainConfigs;
+        case SEG_MODE_GEMM_BF16:
+        case SEG_MODE_GEMM_TF32: return gemm_num_configs();
+    }
+    return 0;
+}
+
+seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_config: atlas is NULL");
+    const int nc = seg_num_configs(mode);
+    if (nc <= 0) return fail(SEG_ERR_INVALID_ARG, "seg_set_config: unknown mode %d", (int)mode);
+    if (config < 0 || config >= nc)
+        return fail(SEG_ERR_INVALID_ARG, "seg_set_config: config %d outside [0,%d)", config, nc);
+    atlas->config[(int)mode] = config;
+    return SEG_OK;
+}
+
+seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config) {
+    g_last_error.clear();
+    if (!atlas || !config) return fail(SEG_ERR_INVALID_ARG, "seg_get_config: NULL argument");
+    if (seg_num_configs(mode) <= 0)
+        return fail(SEG_ERR_INVALID_ARG, "seg_get_config: unknown mode %d", (int)mode);
+    *config = atlas->config[(int)mode];
+    return SEG_OK;
+}
+
+seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_sync_status: atlas is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(st)) ||
+        (e = cudaMemcpy(&h, atlas->status, sizeof(unsigned), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemset(atlas->status, 0, sizeof(unsigned))))
+        return cuda_fail(e, "seg_sync_status");
+    if (h & ST_TIMEOUT) return fail(SEG_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (h & ST_OVERFLOW) return fail(SEG_ERR_OVERFLOW, "a device list overflowed");
+    return SEG_OK;
+}
+
+seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
+                          int64_t* overflow_fibers) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_stats: atlas is NULL");
+    long long h[3] = {0, 0, 0};
+    if (atlas->gemm.stats) {
+        cudaError_t e = cudaMemcpy(h, atlas->gemm.stats, sizeof(h), cudaMemcpyDeviceToHost);
+        if (e) return cuda_fail(e, "seg_gemm_stats");
+    }
+    if (pairs) *pairs = h[0];
+    if (survivors) *survivors = h[1];
+    if (overflow_fibers) *overflow_fibers = h[2];
+    return SEG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Host-side internals shared by the libseg sources: atlas-owned scratch, the tensor-core
+// prune's operands, the batch graph cache and the launchers.
+#pragma once
+
+#include <cstdarg>
+#include <cmath>
+#include <mutex>
+
+#include "seg_common.cuh"
+
+namespace seg {
+
+seg_status fail(seg_status s, const char* fmt, ...);
+seg_status cuda_fail(cudaError_t e, const char* what);
+
+// A growable device buffer owned by an atlas. Users lock the atlas mutex on the host and order
+// themselves on the device through `last_use`, so calls from different streams never overlap
+// on it.
+struct ScratchArena {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t last_use = nullptr;
+};
+seg_status scratch_acquire(ScratchArena* s, size_t bytes, cudaStream_t st, void** out);
+seg_status scratch_release(ScratchArena* s, cudaStream_t st);
+void free_scratch(ScratchArena* s);
+
+// Operands of the tensor-core prune (SEG_MODE_GEMM_*), built with the atlas.
+struct GemmAtlas {
+    int cols = 0;             // 2M columns: sorted centroid s direct at 2s, reversed at 2s+1
+    int cols_pad = 0;         // cols rounded up to the N tile
+    void* b_bf16 = nullptr;   // [cols_pad][64] bf16, centred, K-major
+    void* b_tf32 = nullptr;   // [cols_pad][64] fp32 holding TF32-rounded values
+    long long* stats = nullptr;  // [3] pairs, survivors, overflow fibers of the last call
+};
+seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st);
+void free_gemm_atlas(GemmAtlas* g);
+int gemm_num_configs();
+seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,
+                      const float* fib, long long n, bool tf32, int* labels, float* dist,
+                      int* cidx, unsigned char* orient, cudaStream_t st);
+
+// Cached CUDA graph of the batched launch.
+struct BatchState {
+    void* graph_exec = nullptr;  // cudaGraphExec_t
+    int nsubj = 0;
+    int mode = -1;
+    void* table = nullptr;        // device work table
+    size_t table_bytes = 0;
+    void* counter = nullptr;      // device work counter
+};
+void free_batch(BatchState* b);
+seg_status batch_launch(const AtlasView& at, GemmAtlas* g, BatchState* b, ScratchArena* scratch,
+                        std::mutex* mu, int nsubj, const float* const* fib,
+                        const long long* counts, int mode, int* const* labels,
+                        float* const* dist, cudaStream_t st);
+
+seg_status grad_launch(const AtlasView& at, const int* inv_perm, ScratchArena* scratch,
+                       std::mutex* mu, const float* fib, long long n, const double* h_aff,
+                       const int* cidx, const unsigned char* orient, double* grad_aff,
+                       float* grad_cen, double* cost, cudaStream_t st);
+seg_status apply_affine_launch(const float* in, long long n, const double* h_aff, float* out,
+                               cudaStream_t st);
+
+}  // namespace seg

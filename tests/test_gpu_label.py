@@ -1,0 +1,137 @@
+"""GPU parity of seg_label (C ABI through the ctypes binding) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1912_11494_gb300 import binding, synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["plain"]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1912_11494_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def make_atlas(cen, bo, thr, dev):
+    return binding.Atlas(torch.as_tensor(np.ascontiguousarray(cen, np.float32), device=dev),
+                         torch.as_tensor(np.ascontiguousarray(bo, np.int32), device=dev),
+                         torch.as_tensor(np.ascontiguousarray(thr, np.float32), device=dev))
+
+
+def run(atlas, fib, dev, mode):
+    f = torch.as_tensor(np.ascontiguousarray(fib, np.float32), device=dev)
+    lab, dist, cidx, orient = binding.label(atlas, f, mode)
+    binding.seg_sync_status(atlas)
+    return lab.cpu().numpy(), dist.cpu().numpy(), cidx.cpu().numpy(), orient.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_small_workload_parity(dev, small_workload, mode):
+    atlas_np, fib = small_workload
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    lab, dist, cidx, orient = run(at, fib, dev, mode)
+    res = parity.compare(fib, atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, lab,
+                         dist, cidx, orient)
+    assert res["labelled"] > 0.5 * len(fib)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,M", [(1, 1), (31, 20), (32, 257), (33, 20), (1000, 257),
+                                 (129, 1), (300, 513)])
+def test_ragged_shapes(dev, n, M, mode):
+    rng = np.random.default_rng(n * 1000 + M)
+    nb = max(1, M // 20)
+    cen = synth.make_atlas(nb, per_bundle=M // nb + 1, seed=6000 + M).centroids[:M]
+    bo = (np.arange(M) % nb).astype(np.int32)
+    rng.shuffle(bo)  # bundles interleaved in the caller's order
+    thr = rng.uniform(5, 8, size=nb).astype(np.float32)
+    src = cen[rng.integers(0, M, size=n)] + rng.normal(0, 1.5, size=(n, 21, 3))
+    src[::2] = src[::2, ::-1]
+    fib = src.astype(np.float32)
+    at = make_atlas(cen, bo, thr, dev)
+    lab, dist, cidx, orient = run(at, fib, dev, mode)
+    parity.compare(fib, cen, bo, thr, lab, dist, cidx, orient)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_degenerate_cases(dev, mode):
+    a = synth.make_atlas(10, per_bundle=5, seed=77)
+    cen, bo = a.centroids, a.bundle_of
+    # fibers exactly on centroids, reversed copies, a non-finite fiber, a far fiber
+    fib = np.concatenate([cen[:7], cen[7:14, ::-1], cen[:2] + 500.0]).astype(np.float32)
+    fib[3, 5, 1] = np.nan
+    fib[4, 0, 0] = np.inf
+    for thr in (a.thresholds, np.full(10, 1e-3, np.float32), np.full(10, 1e4, np.float32)):
+        at = make_atlas(cen, bo, thr, dev)
+        lab, dist, cidx, orient = run(at, fib, dev, mode)
+        parity.compare(fib, cen, bo, thr, lab, dist, cidx, orient)
+        assert lab[3] == -1 and np.isnan(dist[3]) and lab[4] == -1
+        assert dist[0] == 0.0 and dist[8] == 0.0 and orient[8] == 1
+    # every fiber far from everything: all unlabelled
+    at = make_atlas(cen, bo, a.thresholds, dev)
+    lab, dist, _, _ = run(at, fib[-2:], dev, mode)
+    assert np.all(lab == -1) and np.all(np.isinf(dist))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_exact_ties_lowest_bundle_then_centroid(dev, mode):
+    t = np.arange(21, dtype=np.float32)
+    base = np.stack([t, 0 * t, 0 * t], axis=1)
+    offs = [(0, 0, 2), (0, 2, 0), (0, -2, 0), (0, 0, -2), (2, 0, 0)]  # all exactly 2
+    cen = np.stack([base + np.array(o, np.float32) for o in offs])
+    bo = np.array([3, 1, 1, 2, 0], np.int32)  # every centroid at distance 2
+    thr = np.full(4, 5.0, np.float32)
+    at = make_atlas(cen, bo, thr, dev)
+    lab, dist, cidx, orient = run(at, base[None].repeat(40, 0), dev, mode)
+    assert np.all(lab == 0) and np.all(cidx == 4) and np.all(dist == 2.0)
+    bo2 = np.array([3, 1, 1, 2, 3], np.int32)
+    at = make_atlas(cen, bo2, thr, dev)
+    lab, dist, cidx, orient = run(at, base[None].repeat(40, 0), dev, mode)
+    assert np.all(lab == 1) and np.all(cidx == 1)
+
+
+def test_empty_input(dev):
+    a = synth.make_atlas(3, per_bundle=2, seed=1)
+    at = make_atlas(a.centroids, a.bundle_of, a.thresholds, dev)
+    binding.seg_label(at, None, "plain", None, n=0)
+    binding.seg_sync_status(at)
+
+
+def test_invalid_atlas_rejected(dev):
+    a = synth.make_atlas(3, per_bundle=2, seed=1)
+    bad = a.bundle_of.copy()
+    bad[0] = 7
+    with pytest.raises(binding.SegError):
+        make_atlas(a.centroids, bad, a.thresholds, dev)
+    thr = a.thresholds.copy()
+    thr[1] = -1
+    with pytest.raises(binding.SegError):
+        make_atlas(a.centroids, a.bundle_of, thr, dev)
+    cen = a.centroids.copy()
+    cen[2, 3, 1] = np.nan
+    with pytest.raises(binding.SegError):
+        make_atlas(cen, a.bundle_of, a.thresholds, dev)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_sampled_parity(dev, mode):
+    """4,145,000 fibers x 10,000 centroids labelled in one call (the benchmark's launch);
+    3,000 sampled fibers are checked one by one against the oracle."""
+    atlas_np, fib = synth.workload("subject4145k_atlas10k", device="cuda")
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    lab, dist, cidx, orient = run(at, fib, dev, mode)
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(len(fib), size=3000, replace=False))
+    idx = np.concatenate([idx, np.arange(len(fib) - 37, len(fib))])  # the ragged tail
+    res = parity.compare(fib[idx], atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds,
+                         lab[idx], dist[idx], cidx[idx], orient[idx])
+    assert res["labelled"] > 0.6 * len(idx)
+    frac = (lab >= 0).mean()
+    assert 0.6 < frac < 0.9
