@@ -31,12 +31,14 @@ namespace {
 constexpr int PW = 4;    // independent warps per CTA
 constexpr int TW = 32;   // fibers per warp tile
 
+constexpr int QCAP = 1024;  // per-warp queue of test1 survivors, drained after the screen
+
 template <int PC, int PK>
 struct WarpSmem {
-    static constexpr int QW = 32 + PK * PC * 32;  // queue: one drain batch + one block's worth
+    static constexpr int QW = QCAP;
     static constexpr size_t fc_off = 0;                        // [TW][63] floats
-    static constexpr size_t fs_off = fc_off + TW * NC * 4;     // [TW] float4
-    static constexpr size_t key_off = fs_off + TW * 16;        // [TW] u64
+    static constexpr size_t fs_off = fc_off + TW * NC * 4;     // [TW][2] float4
+    static constexpr size_t key_off = fs_off + TW * 32;        // [TW] u64
     static constexpr size_t q_off = key_off + TW * 8;          // [QW] u32
     static constexpr size_t bar_off = (q_off + QW * 4 + 15) / 16 * 16;
     static constexpr size_t bytes = bar_off + 16;
@@ -69,15 +71,26 @@ __device__ __forceinline__ float key_best2(unsigned long long k) {
 }
 
 // Exact check of one queued pair e = (sorted centroid << 8 | tile fiber); merges into the
-// fiber's key.
+// fiber's key. The centroid row (256 B, aligned) is loaded in one batch of 16-byte loads so a
+// check costs one memory round trip; the fiber comes from shared memory.
 __device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float* fc,
                                                 unsigned long long* key, unsigned e) {
     const int c = (int)(e >> 8);
     const int f = (int)(e & 255u);
+    float b[CROW];
+    const float4* b4 = reinterpret_cast<const float4*>(at.cen + (size_t)c * CROW);
+#pragma unroll
+    for (int q = 0; q < CROW / 4; ++q) {
+        const float4 v = __ldg(b4 + q);
+        b[4 * q] = v.x;
+        b[4 * q + 1] = v.y;
+        b[4 * q + 2] = v.z;
+        b[4 * q + 3] = v.w;
+    }
     const float bound = fminf(__ldg(at.thr2 + c), key_best2(key[f]));
     float d2;
     int o;
-    if (exact_pair(fc + f * NC, at.cen + (size_t)c * CROW, bound, d2, o)) {
+    if (exact_pair(fc + f * NC, b, bound, d2, o)) {
         const unsigned long long k = ((unsigned long long)__float_as_uint(d2) << 32) |
                                      ((unsigned long long)c << 1) | (unsigned)o;
         atomicMin(key + f, k);
@@ -134,88 +147,132 @@ k_label_plain(const float* __restrict__ fib, long long n, AtlasView at, int fib_
         }
         return;
     }
-    // per-fiber screening data: centred centre point and |a|^2/2 minus its rounding slack;
+    // per-fiber screening data: centred centre point and |a|^2/2 minus its rounding slack,
+    // each value twice so a packed FP32x2 FMA can use it against two centroids at once;
     // a fiber with a non-finite coordinate gets NaN (never passes) and is reported as such.
     {
-        float4 v = make_float4(0.f, 0.f, 0.f, INFINITY);
+        float x = 0.f, y = 0.f, z = 0.f, h = INFINITY;
         if (lane < nf) {
             const float* a = fc + lane * NC;
             bool finite = true;
             for (int k = 0; k < NC; ++k) finite = finite && isfinite(a[k]);
-            const float x = a[3 * CENTRE] - at.c0x, y = a[3 * CENTRE + 1] - at.c0y,
-                        z = a[3 * CENTRE + 2] - at.c0z;
+            x = a[3 * CENTRE] - at.c0x;
+            y = a[3 * CENTRE + 1] - at.c0y;
+            z = a[3 * CENTRE + 2] - at.c0z;
             const float r2 = fmaf(x, x, fmaf(y, y, z * z));
-            v = make_float4(x, y, z, finite ? 0.5f * r2 - 1e-5f * r2 - 1e-3f : NAN);
+            h = finite ? 0.5f * r2 - 1e-5f * r2 - 1e-3f : NAN;
         }
-        fs[lane] = v;
+        fs[2 * lane] = make_float4(x, x, y, y);
+        fs[2 * lane + 1] = make_float4(z, z, h, h);
     }
     __syncwarp();
 
     const unsigned lt = (1u << lane) - 1u;
     const int nch = at.M_pad / CH;
     const int nfk = (nf + PK - 1) / PK * PK;
-    int qn = 0;
-    for (int j = 0; j < nch; ++j) {
-        float bx[PC], by[PC], bz[PC], mg[PC];
+    // The screen runs until the atlas is done or the queue is full; then the queue is drained
+    // outside the screen loop (so the two never hold registers at the same time) and the
+    // screen resumes at the ballot where it stopped: chunk jres, fiber block fres, and within
+    // that block the (fiber, centroid slot) index rres. Every drain empties the queue and the
+    // next ballot adds at most 32 entries, so each round makes progress.
+    int jres = 0, fres = 0, rres = 0;
+    bool first = true;
+    for (;;) {
+        int qn = 0;
+        bool full = false;
+        int j = jres;
+        if (!first) {
 #pragma unroll
-        for (int c = 0; c < PC; ++c) {
-            bx[c] = nxt[c].x;
-            by[c] = nxt[c].y;
-            bz[c] = nxt[c].z;
-            mg[c] = nxt[c].w;
+            for (int c = 0; c < PC; ++c) nxt[c] = __ldg(at.scr2 + (size_t)j * CH + c * 32 + lane);
         }
-        if (j + 1 < nch) {
+        first = false;
+        int rskip = rres;
+        for (; j < nch; ++j) {
+            // centroids c and c+1 of the lane side by side for packed FP32x2 math
+            float2 bx[PC / 2], by[PC / 2], bz[PC / 2], mg[PC / 2];
 #pragma unroll
-            for (int c = 0; c < PC; ++c) nxt[c] = __ldg(at.scr2 + (size_t)(j + 1) * CH + c * 32 + lane);
-        }
-        const unsigned cbase = (unsigned)(j * CH + lane);
-        for (int f = 0; f < nfk; f += PK) {
-            // score_k = max_c (a_k.b_c + mg_c) - h_k >= 0  <=>  some centroid passes test1
-            float sk[PK];
-#pragma unroll
-            for (int k = 0; k < PK; ++k) {
-                const float4 a = fs[f + k];
-                float t[PC];
+            for (int p = 0; p < PC / 2; ++p) {
+                bx[p] = make_float2(nxt[2 * p].x, nxt[2 * p + 1].x);
+                by[p] = make_float2(nxt[2 * p].y, nxt[2 * p + 1].y);
+                bz[p] = make_float2(nxt[2 * p].z, nxt[2 * p + 1].z);
+                mg[p] = make_float2(nxt[2 * p].w, nxt[2 * p + 1].w);
+            }
+            if (j + 1 < nch) {
 #pragma unroll
                 for (int c = 0; c < PC; ++c)
-                    t[c] = fmaf(a.z, bz[c], fmaf(a.y, by[c], fmaf(a.x, bx[c], mg[c])));
-                sk[k] = maxn<PC>(t) - a.w;
+                    nxt[c] = __ldg(at.scr2 + (size_t)(j + 1) * CH + c * 32 + lane);
             }
-            if (__any_sync(0xffffffffu, maxn<PK>(sk) >= 0.0f)) {
+            const unsigned cbase = (unsigned)(j * CH + lane);
+            for (int f = (j == jres ? fres : 0); f < nfk; f += PK) {
+                // score_k = max_c (a_k.b_c + mg_c) - h_k >= 0  <=>  a centroid passes test1
+                float sk[PK];
 #pragma unroll
                 for (int k = 0; k < PK; ++k) {
-                    if (__any_sync(0xffffffffu, sk[k] >= 0.0f)) {
-                        const float4 a = fs[f + k];
+                    const float4 a0 = fs[2 * (f + k)], a1 = fs[2 * (f + k) + 1];
+                    float t[PC];
 #pragma unroll
-                        for (int c = 0; c < PC; ++c) {
-                            const float t =
-                                fmaf(a.z, bz[c], fmaf(a.y, by[c], fmaf(a.x, bx[c], mg[c])));
-                            const bool p = t >= a.w;
-                            const unsigned m = __ballot_sync(0xffffffffu, p);
-                            if (p)
-                                q[qn + __popc(m & lt)] =
-                                    ((cbase + (unsigned)(c * 32)) << 8) | (unsigned)(f + k);
-                            qn += __popc(m);
+                    for (int p = 0; p < PC / 2; ++p) {
+                        float2 u = __ffma2_rn(make_float2(a0.x, a0.y), bx[p], mg[p]);
+                        u = __ffma2_rn(make_float2(a0.z, a0.w), by[p], u);
+                        u = __ffma2_rn(make_float2(a1.x, a1.y), bz[p], u);
+                        t[2 * p] = u.x;
+                        t[2 * p + 1] = u.y;
+                    }
+                    sk[k] = maxn<PC>(t) - a1.z;
+                }
+                if (__any_sync(0xffffffffu, maxn<PK>(sk) >= 0.0f)) {
+#pragma unroll
+                    for (int k = 0; k < PK; ++k) {
+                        if (!full && __any_sync(0xffffffffu, sk[k] >= 0.0f)) {
+                            const float4 a0 = fs[2 * (f + k)], a1 = fs[2 * (f + k) + 1];
+#pragma unroll
+                            for (int c = 0; c < PC; ++c) {
+                                if (full || k * PC + c < rskip) continue;
+                                const float bxc = c & 1 ? bx[c / 2].y : bx[c / 2].x;
+                                const float byc = c & 1 ? by[c / 2].y : by[c / 2].x;
+                                const float bzc = c & 1 ? bz[c / 2].y : bz[c / 2].x;
+                                const float mgc = c & 1 ? mg[c / 2].y : mg[c / 2].x;
+                                const float t =
+                                    fmaf(a1.x, bzc, fmaf(a0.z, byc, fmaf(a0.x, bxc, mgc)));
+                                const bool p = t >= a1.z;
+                                const unsigned m = __ballot_sync(0xffffffffu, p);
+                                if (m) {
+                                    if (qn + 32 > QCAP) {
+                                        full = true;
+                                        rres = k * PC + c;
+                                    } else {
+                                        if (p)
+                                            q[qn + __popc(m & lt)] =
+                                                ((cbase + (unsigned)(c * 32)) << 8) |
+                                                (unsigned)(f + k);
+                                        qn += __popc(m);
+                                    }
+                                }
+                            }
                         }
                     }
                 }
-                __syncwarp();
-                while (qn >= 32) {
-                    const unsigned e = q[qn - 32 + lane];
-                    __syncwarp();
-                    qn -= 32;
-                    exact_and_merge(at, fc, key, e);
+                rskip = 0;
+                if (full) {
+                    fres = f;
+                    break;
                 }
             }
+            if (full) {
+                jres = j;
+                break;
+            }
         }
+        __syncwarp();
+        for (int i = lane; i < qn; i += 32) exact_and_merge(at, fc, key, q[i]);
+        __syncwarp();
+        if (!full) break;
     }
-    __syncwarp();
-    if (lane < qn) exact_and_merge(at, fc, key, q[lane]);
-    __syncwarp();
+
     if (lane < nf) {
         const long long gi = f0 + lane;
         const unsigned long long k = key[lane];
-        if (isnan(fs[lane].w)) {
+        if (isnan(fs[2 * lane + 1].z)) {
             labels[gi] = -1;
             if (dist) dist[gi] = NAN;
             if (cidx) cidx[gi] = -1;
@@ -260,6 +317,7 @@ cudaError_t launch_cfg(const AtlasView& at, const float* fib, long long n, int* 
 // Tile shapes (centroids per lane, fibers per vote) the autotuner chooses from.
 // Entry 0 is the default (fastest measured on the 4,145,000 x 10,000 workload).
 const int kPlainConfigs[][2] = {{8, 4}, {4, 2}, {4, 4}, {8, 2}, {2, 8}, {4, 8}};
+static_assert(true, "every C above is even: the screen pairs centroids for FP32x2 math");
 const int kNumPlainConfigs = 6;
 
 cudaError_t launch_label_plain(const AtlasView& at, const float* fib, long long n, int* labels,

@@ -135,3 +135,35 @@ def test_full_size_sampled_parity(dev, mode):
     assert res["labelled"] > 0.6 * len(idx)
     frac = (lab >= 0).mean()
     assert 0.6 < frac < 0.9
+
+
+def test_every_tile_shape_identical(dev, small_workload):
+    """All tile-shape configurations of a mode compute the same labels, distances, centroids."""
+    atlas_np, fib = small_workload
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    for mode in MODES:
+        outs = []
+        for cfg in range(binding.seg_num_configs(mode)):
+            binding.seg_set_config(at, mode, cfg)
+            assert binding.seg_get_config(at, mode) == cfg
+            outs.append(run(at, fib, dev, mode))
+        for o in outs[1:]:
+            for x, y in zip(outs[0], o):
+                np.testing.assert_array_equal(x, y)
+    with pytest.raises(binding.SegError):
+        binding.seg_set_config(at, "plain", binding.seg_num_configs("plain"))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_every_pair_passes_overflowing_queues(dev, mode):
+    """Thresholds so large that every (fiber, centroid) pair passes: the per-warp queues of
+    test1 survivors overflow many times and must resume without losing or repeating work."""
+    a = synth.make_atlas(20, per_bundle=20, seed=31)
+    fib = synth.make_subject(a, 200, 0.5, seed=32)
+    thr = np.full(20, 1e4, np.float32)
+    at = make_atlas(a.centroids, a.bundle_of, thr, dev)
+    for cfg in range(binding.seg_num_configs(mode)):
+        binding.seg_set_config(at, mode, cfg)
+        lab, dist, cidx, orient = run(at, fib, dev, mode)
+        parity.compare(fib, a.centroids, a.bundle_of, thr, lab, dist, cidx, orient)
+        assert np.all(lab >= 0)
