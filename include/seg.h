@@ -150,6 +150,24 @@ seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                     void* stream);
 
 /*
+ * seg_grad without any device allocation, for callers that cannot allocate: code running
+ * inside a host allocator callback or a plugin whose host framework owns all device memory,
+ * or a process whose device memory is reserved up front. The paper has no counterpart.
+ * Arguments, outputs and results are those of seg_grad (the FP64 sums use a different fixed
+ * order, so results agree to rounding, not bit for bit). The scratch is a fixed 1.7 MB array
+ * inside the library, held by every GPU that loads it until the process exits:
+ *  - n may be at most 4,194,304 fibers per call; larger n returns SEG_ERR_INVALID_ARG;
+ *  - calls share that array, so calls whose work overlaps on the GPU race: serialize them;
+ *  - the first call on each device looks up the array's device address (cudaGetSymbolAddress
+ *    with that device current); make that first call before any stream capture.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                            const double* h_affine12, const int32_t* d_cidx,
+                            const uint8_t* d_orient, double* d_grad_affine12,
+                            float* d_grad_centroids, double* d_cost, void* stream);
+
+/*
  * Tile shapes of a mode's kernels (the autotuner's search space; not in the paper).
  * seg_num_configs returns how many shapes `mode` has (>= 1). seg_set_config selects shape
  * `config` in [0, seg_num_configs(mode)) for later calls on this atlas; 0 is the default. Every

@@ -34,6 +34,7 @@ SIGNATURES = [
     ("seg_label_batch", ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_int, _P, _P, _P]),
     ("seg_apply_affine", ctypes.c_int, [_P, _I64, _P, _P, _P]),
     ("seg_grad", ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    ("seg_grad_noalloc", ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     ("seg_sync_status", ctypes.c_int, [_P, _P]),
     ("seg_num_configs", ctypes.c_int32, [ctypes.c_int]),
     ("seg_set_config", ctypes.c_int, [_P, ctypes.c_int, _I32]),
@@ -208,6 +209,18 @@ def seg_get_config(atlas: Atlas, mode) -> int:
     v = ctypes.c_int32()
     _check(lib().seg_get_config(atlas.handle, _mode(mode), ctypes.byref(v)))
     return v.value
+
+
+def seg_grad_noalloc(atlas: Atlas, fibers, affine12, cidx, orient, grad_affine,
+                     grad_centroids=None, cost=None, stream=None):
+    """seg_grad for callers that cannot allocate device memory (fixed in-library scratch;
+    at most 4,194,304 fibers per call; overlapping calls race)."""
+    buf = _affine_buf(affine12)
+    n = 0 if fibers is None else int(fibers.shape[0])
+    _check(lib().seg_grad_noalloc(atlas.handle, _ptr(fibers), n,
+                                  ctypes.cast(buf, ctypes.c_void_p), _ptr(cidx), _ptr(orient),
+                                  _ptr(grad_affine), _ptr(grad_centroids), _ptr(cost),
+                                  _stream(stream)))
 
 
 def seg_sync_status(atlas: Atlas, stream=None):

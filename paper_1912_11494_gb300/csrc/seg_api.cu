@@ -347,6 +347,22 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
     return SEG_OK;
 }
 
+seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                            const double* h_affine12, const int32_t* d_cidx,
+                            const uint8_t* d_orient, double* d_grad_affine12,
+                            float* d_grad_centroids, double* d_cost, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: n < 0");
+    if (!h_affine12 || !d_grad_affine12)
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: NULL affine or gradient buffer");
+    if (n > 0 && (!d_fibers || !d_cidx || !d_orient))
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: NULL fibers, cidx or orient");
+    return grad_noalloc_launch(atlas->view, atlas->inv_perm, d_fibers, n, h_affine12, d_cidx,
+                               d_orient, d_grad_affine12, d_grad_centroids, d_cost,
+                               (cudaStream_t)stream);
+}
+
 seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_sync_status: atlas is NULL");

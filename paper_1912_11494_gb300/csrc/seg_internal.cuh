@@ -59,6 +59,10 @@ seg_status grad_launch(const AtlasView& at, const int* inv_perm, ScratchArena* s
                        std::mutex* mu, const float* fib, long long n, const double* h_aff,
                        const int* cidx, const unsigned char* orient, double* grad_aff,
                        float* grad_cen, double* cost, cudaStream_t st);
+seg_status grad_noalloc_launch(const AtlasView& at, const int* inv_perm, const float* fib,
+                               long long n, const double* h_aff, const int* cidx,
+                               const unsigned char* orient, double* grad_aff, float* grad_cen,
+                               double* cost, cudaStream_t st);
 seg_status apply_affine_launch(const float* in, long long n, const double* h_aff, float* out,
                                cudaStream_t st);
 
