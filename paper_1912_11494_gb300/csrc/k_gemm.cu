@@ -1,17 +1,628 @@
-// SEG_MODE_GEMM_*: tensor-core lower-bound prune + exact re-check (placeholder until built).
+// SEG_MODE_GEMM_BF16 / SEG_MODE_GEMM_TF32: tensor-core lower-bound prune, then the exact FP32
+// test on the survivors only. Not in the paper; labels and distances equal SEG_MODE_PLAIN's.
+//
+// Bound. For a fiber a and a centroid b taken in orientation o (points in order, or reversed as
+// in Eq. 2), with p, q their 63 coordinates (centred by the same offset),
+//     d_o^2 = max_i |a_i - b_o(i)|^2 >= (1/21) sum_i |a_i - b_o(i)|^2 = S / 21,
+//     S = |p|^2 + |q|^2 - 2 p.q,
+// so S > 21 theta^2 proves the orientation fails its threshold. p.q for all fibers x all 2M
+// (centroid, orientation) columns is one GEMM [n x 64] x [64 x 2M] on the tensor cores, with the
+// operands rounded to BF16 (or TF32) and FP32 accumulation in tensor memory. The rounding error
+// |p.q - p~.q~| <= kappa |p||q| <= kappa (|p|^2 + |q|^2) / 2 (kappa = 2u + u^2 + accumulation)
+// is separable, so the test folds into one compare per element:
+//     keep (fiber i, column j)  <=>  p~_i.q~_j + pad_j >= alpha_i,
+//     alpha_i = (1 - kappa)/2 |p_i|^2 - slack_i,
+//     pad_j   >= -[(|q_j|^2 - 21 theta_j^2 (1 + rho)) / 2 - kappa/2 |q_j|^2 - slack_j],
+// where pad_j is the 64th K column of the centroid operand (the fiber operand holds 1 there) and
+// is rounded upward, and the slacks cover FP32 norms, the centring and the exact test's own
+// rounding (rho). Every pair the exact FP32 test would accept therefore survives the prune.
+//
+// Kernel. A persistent CTA per SM, warp-specialised: warp 0 issues TMA loads (R fiber tiles of
+// 128 rows per work unit, double-buffered, and a ring of S centroid tiles of N columns), warp 1
+// issues tcgen05.mma (M=128, N, K=64) into one of two TMEM accumulators of R*N columns, and warps
+// 2..5 read the other accumulator with tcgen05.ld.red, which returns each row's max over 32
+// columns: only when that max reaches alpha does the warp look at the individual values and
+// append the surviving (fiber, column) pairs to a global list (staged per warp in shared memory).
+// A second kernel runs the exact test of Section 2.3 on every survivor in its orientation and
+// merges the result into the fiber's packed key with atomicMin (same key as the plain kernel,
+// so the tie rule of Algorithm 1 holds); fibers whose survivors did not fit the list are
+// rescanned by an exact kernel; a last kernel writes labels and distances.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "seg_exact.cuh"
 #include "seg_internal.cuh"
+#include "seg_tc.cuh"
 
 namespace seg {
+namespace {
 
-seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st) {
-    (void)at;
-    (void)st;
-    cudaError_t e = cudaMalloc(&g->stats, 3 * sizeof(long long));
-    if (e) return cuda_fail(e, "gemm stats");
-    return cudaMemsetAsync(g->stats, 0, 3 * sizeof(long long), st) ? SEG_ERR_CUDA : SEG_OK;
+constexpr int GEMM_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int COL_ALIGN = 256;     // columns padded to a multiple of this
+constexpr int STAGE_CAP = 256;     // survivors staged per epilogue warp
+constexpr unsigned long long NAN_KEY = ~0ull - 1ull;
+constexpr float PAD_NEG = -1e30f;  // pad of padding columns: never survives
+
+// Rounding constants: unit roundoff of the operand format and the FP32 accumulation bound for
+// 64 terms (taken as 64 ulps, conservative for any summation order of the tensor core).
+constexpr double U_BF16 = 1.0 / 512.0;    // 2^-9, round to nearest
+constexpr double U_TF32 = 1.0 / 2048.0;   // 2^-11, round to nearest
+constexpr double GAMMA_ACC = 64.0 / 8388608.0;
+constexpr double RHO = 1e-5;              // relative slack for the exact test's FP32 rounding
+
+__host__ __device__ inline double kappa_of(int fmt) {
+    const double u = fmt == 1 ? U_BF16 : U_TF32;
+    return 1.05 * (2.0 * u + u * u) + 2.0 * GAMMA_ACC;
 }
 
-int gemm_num_configs() { return 1; }
+struct GemmScratch {
+    void* a;                      // fiber operand [n_pad][64]
+    float* alpha;                 // [n_pad]
+    unsigned long long* key;      // [n]
+    unsigned char* flag;          // [n] survivors dropped for lack of list space
+    uint2* list;                  // [cap] (fiber, column)
+    unsigned long long* cnt;      // [0] survivors appended, [1] fibers flagged
+    long long cap;
+};
+
+// ---- operand preparation ---------------------------------------------------------------------
+
+__device__ inline float tf32_rn(float x) {
+    uint32_t u = __float_as_uint(x);
+    u = (u + 0x1000u) & 0xFFFFE000u;  // round to nearest (ties away) at 10 mantissa bits
+    return __uint_as_float(u);
+}
+
+__device__ inline float tf32_up(float x) {  // round toward +inf at 10 mantissa bits
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x1FFFu) == 0u) return x;
+    if (x > 0.0f) u = (u + 0x2000u) & 0xFFFFE000u;
+    else u &= 0xFFFFE000u;
+    return __uint_as_float(u);
+}
+
+// Centroid columns: sorted centroid s gives column 2s (points in order) and 2s+1 (reversed).
+__global__ void k_prep_b(AtlasView at, int fmt, int cols, int cols_pad, void* out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols_pad) return;
+    float q[NC];
+    float pad = PAD_NEG;
+    if (j < cols) {
+        const int s = j >> 1, o = j & 1;
+        const float* b = at.cen + (size_t)s * CROW;
+        double n2 = 0.0;
+        for (int i = 0; i < NPTS; ++i) {
+            const int pi = o ? NPTS - 1 - i : i;
+            q[3 * i] = b[3 * pi] - at.c0x;
+            q[3 * i + 1] = b[3 * pi + 1] - at.c0y;
+            q[3 * i + 2] = b[3 * pi + 2] - at.c0z;
+            n2 += (double)q[3 * i] * q[3 * i] + (double)q[3 * i + 1] * q[3 * i + 1] +
+                  (double)q[3 * i + 2] * q[3 * i + 2];
+        }
+        const double t2 = (double)at.thr2[s];
+        const double kap = kappa_of(fmt);
+        const double G = 0.5 * (n2 - 21.0 * t2 * (1.0 + RHO)) - 0.5 * kap * n2 -
+                         (1e-5 * (n2 + 21.0 * t2) + 0.005);
+        pad = (float)(-G);
+        // round the float upward so the pad never undershoots -G
+        if ((double)pad < -G) pad = nextafterf(pad, INFINITY);
+    } else {
+        for (int k = 0; k < NC; ++k) q[k] = 0.0f;
+    }
+    if (fmt == 1) {
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)j * 64;
+        for (int k = 0; k < NC; ++k) o[k] = __float2bfloat16_rn(q[k]);
+        o[63] = j < cols ? __float2bfloat16_ru(pad) : __float2bfloat16_rn(PAD_NEG);
+    } else {
+        float* o = reinterpret_cast<float*>(out) + (size_t)j * 64;
+        for (int k = 0; k < NC; ++k) o[k] = tf32_rn(q[k]);
+        o[63] = j < cols ? tf32_up(pad) : tf32_rn(PAD_NEG);
+    }
+}
+
+// Fiber rows: centred coordinates, 1 in the pad column, alpha_i; keys initialised.
+__global__ void k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView at,
+                         int fmt, void* __restrict__ out, float* __restrict__ alpha,
+                         unsigned long long* __restrict__ key) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    float p[NC];
+    bool finite = i < n;
+    double n2 = 0.0;
+    if (i < n) {
+        const float* a = fib + i * NC;
+        for (int k = 0; k < NC; ++k) finite = finite && isfinite(__ldg(a + k));
+        for (int t = 0; t < NPTS; ++t) {
+            p[3 * t] = __ldg(a + 3 * t) - at.c0x;
+            p[3 * t + 1] = __ldg(a + 3 * t + 1) - at.c0y;
+            p[3 * t + 2] = __ldg(a + 3 * t + 2) - at.c0z;
+        }
+    }
+    if (!finite) {
+        for (int k = 0; k < NC; ++k) p[k] = 0.0f;
+    } else {
+        for (int k = 0; k < NC; ++k) n2 += (double)p[k] * p[k];
+    }
+    const double kap = kappa_of(fmt);
+    const double al = 0.5 * (1.0 - kap) * n2 - (1e-5 * n2 + 0.005);
+    alpha[i] = finite ? __double2float_rd(al) : INFINITY;
+    if (i < n) key[i] = finite ? ~0ull : NAN_KEY;
+    if (fmt == 1) {
+        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(
+            reinterpret_cast<__nv_bfloat16*>(out) + (size_t)i * 64);
+        for (int k = 0; k < 31; ++k) o[k] = __floats2bfloat162_rn(p[2 * k], p[2 * k + 1]);
+        o[31] = __floats2bfloat162_rn(p[62], 1.0f);
+    } else {
+        float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + (size_t)i * 64);
+        for (int k = 0; k < 15; ++k)
+            o[k] = make_float4(tf32_rn(p[4 * k]), tf32_rn(p[4 * k + 1]), tf32_rn(p[4 * k + 2]),
+                               tf32_rn(p[4 * k + 3]));
+        o[15] = make_float4(tf32_rn(p[60]), tf32_rn(p[61]), tf32_rn(p[62]), 1.0f);
+    }
+}
+
+// ---- the tensor-core screen ------------------------------------------------------------------
+
+template <int FMT, int R, int N, int S, int ABUF>
+struct GemmCfg {
+    static constexpr int ELEM = FMT == 1 ? 2 : 4;
+    static constexpr int KREG = FMT == 1 ? 1 : 2;             // 128-byte K regions per row
+    static constexpr int KSTEPS = FMT == 1 ? 4 : 8;           // MMA K steps (32 bytes each)
+    static constexpr int A_TILE = 128 * 64 * ELEM;            // one 128-row fiber tile
+    static constexpr int A_REGION = 128 * 128;                // bytes of one K region
+    static constexpr int B_TILE = N * 64 * ELEM;
+    static constexpr int B_REGION = N * 128;
+    static constexpr int ACC_COLS = R * N;                    // TMEM columns per accumulator
+    static constexpr int A_OFF = 0;
+    static constexpr int B_OFF = A_OFF + ABUF * R * A_TILE;
+    static constexpr int ST_OFF = B_OFF + S * B_TILE;         // survivor staging
+    static constexpr int BAR_OFF = ST_OFF + 4 * STAGE_CAP * 8;
+    static constexpr int NBAR = 2 * ABUF + 2 * S + 5;
+    static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16 + 1024;  // + alignment slack
+    static_assert(2 * ACC_COLS <= 512, "two accumulators must fit TMEM");
+    static_assert(N % 32 == 0 && N >= 32 && N <= 256, "N");
+    static_assert(A_TILE % 1024 == 0 && B_TILE % 1024 == 0, "1024-byte aligned tiles");
+};
+
+struct Waiter {
+    volatile int* abort;
+    unsigned* status;
+    // wait for `parity` on `bar`; false if the CTA is aborting (another role timed out) or this
+    // wait ran past its limit (then it starts the abort)
+    __device__ bool wait(uint64_t* bar, uint32_t parity) const {
+        if (mbar_try_wait(bar, parity)) return true;
+        const uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(bar, parity)) {
+            if (*abort) return false;
+            if (globaltimer_ns() - t0 > 2000000000ull) {
+                *abort = 1;
+                atomicOr(status, ST_TIMEOUT);
+                return false;
+            }
+        }
+        return true;
+    }
+};
+
+__device__ inline void flush_stage(uint2* st, int& scnt, const GemmScratch& g, int lane) {
+    if (scnt == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(g.cnt, (unsigned long long)scnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < scnt; i += 32) {
+        const uint2 e = st[i];
+        if ((long long)(base + i) < g.cap) {
+            g.list[base + i] = e;
+        } else if (g.flag[e.x] == 0) {
+            g.flag[e.x] = 1;
+            atomicAdd(g.cnt + 1, 1ull);
+        }
+    }
+    __syncwarp();
+    scnt = 0;
+}
+
+template <int FMT, int R, int N, int S, int ABUF>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              long long n_units, int n_tiles, int cols, GemmScratch g, unsigned* status) {
+    using C = GemmCfg<FMT, R, N, S, ABUF>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+    uint64_t* a_full = bars;
+    uint64_t* a_empty = bars + ABUF;
+    uint64_t* b_full = bars + 2 * ABUF;
+    uint64_t* b_empty = bars + 2 * ABUF + S;
+    uint64_t* acc_full = bars + 2 * ABUF + 2 * S;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* mma_done = acc_full + 4;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ABUF; ++i) {
+            mbar_init(a_full + i, 1);
+            mbar_init(a_empty + i, 1);
+        }
+        for (int i = 0; i < S; ++i) {
+            mbar_init(b_full + i, 1);
+            mbar_init(b_empty + i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(acc_full + i, 1);
+            mbar_init(acc_empty + i, 4);
+        }
+        mbar_init(mma_done, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&s_tmem, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const Waiter W{&s_abort, status};
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+        int stage = 0;
+        uint32_t b_phase = 0;     // bit s: parity to wait on b_empty[s]
+        uint32_t b_used = 0;      // bit s: stage s received a load
+        uint32_t a_used = 0, a_par = 0;
+        long long it = 0;
+        bool ok = true;
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+            const int ab = ABUF == 2 ? (int)(it & 1) : 0;
+            const long long use = ABUF == 2 ? (it >> 1) : it;  // uses of this A buffer so far
+            if (use > 0) ok = W.wait(a_empty + ab, (uint32_t)((use - 1) & 1));
+            if (!ok) break;
+            a_used |= 1u << ab;
+            a_par = (a_par & ~(1u << ab)) | ((uint32_t)(use & 1) << ab);
+            unsigned char* sA = smem + C::A_OFF + ab * R * C::A_TILE;
+            mbar_arrive_expect_tx(a_full + ab, (uint32_t)(R * C::A_TILE));
+            for (int r = 0; r < R; ++r)
+                for (int kr = 0; kr < C::KREG; ++kr)
+                    tma_load_2d(sA + r * C::A_TILE + kr * C::A_REGION, &tmA, kr * 32,
+                                (int)((u * R + r) * 128), a_full + ab);
+            for (int t = 0; t < n_tiles; ++t) {
+                if (!W.wait(b_empty + stage, ((b_phase >> stage) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                b_phase ^= 1u << stage;
+                b_used |= 1u << stage;
+                unsigned char* sB = smem + C::B_OFF + stage * C::B_TILE;
+                mbar_arrive_expect_tx(b_full + stage, (uint32_t)C::B_TILE);
+                for (int kr = 0; kr < C::KREG; ++kr)
+                    tma_load_2d(sB + kr * C::B_REGION, &tmB, kr * 32, t * N, b_full + stage);
+                stage = stage + 1 == S ? 0 : stage + 1;
+            }
+        }
+        if (s_abort) {
+            // copies this thread issued may still be landing: wait for each buffer's last load
+            // (b_phase bit s flipped once per load, so its complement is the last load's parity)
+            for (int i = 0; i < S; ++i)
+                if ((b_used >> i) & 1u) mbar_wait_bounded(b_full + i, ((b_phase >> i) & 1u) ^ 1u);
+            for (int i = 0; i < ABUF; ++i)
+                if ((a_used >> i) & 1u) mbar_wait_bounded(a_full + i, (a_par >> i) & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = make_idesc(FMT, 128, N);
+        int stage = 0;
+        uint32_t b_phase = 0;
+        long long it = 0, tile = 0;
+        bool ok = true;
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+            const int ab = ABUF == 2 ? (int)(it & 1) : 0;
+            const long long use = ABUF == 2 ? (it >> 1) : it;
+            if (!W.wait(a_full + ab, (uint32_t)(use & 1))) break;
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + C::A_OFF + ab * R * C::A_TILE);
+            for (int t = 0; t < n_tiles; ++t, ++tile) {
+                const int cb = (int)(tile & 1);
+                const long long cuse = tile >> 1;
+                if (!W.wait(b_full + stage, (b_phase >> stage) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                b_phase ^= 1u << stage;
+                if (cuse > 0 && !W.wait(acc_empty + cb, (uint32_t)((cuse - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sB = smem_u32(smem + C::B_OFF + stage * C::B_TILE);
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t d = tmem + (uint32_t)(cb * C::ACC_COLS + r * N);
+#pragma unroll
+                    for (int kk = 0; kk < C::KSTEPS; ++kk) {
+                        const uint32_t koff = (kk / 4) * 0 + (uint32_t)((kk & 3) * 32);
+                        const uint64_t ad = make_sdesc_sw128(sA + r * C::A_TILE +
+                                                             (kk / 4) * C::A_REGION + koff);
+                        const uint64_t bd =
+                            make_sdesc_sw128(sB + (kk / 4) * C::B_REGION + koff);
+                        if (FMT == 1)
+                            mma_f16(d, ad, bd, idesc, kk > 0);
+                        else
+                            mma_tf32(d, ad, bd, idesc, kk > 0);
+                    }
+                }
+                mma_commit(b_empty + stage);
+                mma_commit(acc_full + cb);
+                stage = stage + 1 == S ? 0 : stage + 1;
+            }
+            mma_commit(a_empty + ab);
+        }
+        // every MMA and every commit above has completed once this arrives
+        mma_commit(mma_done);
+        mbar_wait_bounded(mma_done, 0);
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        uint2* st = reinterpret_cast<uint2*>(smem + C::ST_OFF) + (warp - 2) * STAGE_CAP;
+        int scnt = 0;
+        long long tile = 0;
+        bool ok = true;
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            float alpha[R];
+            unsigned fib[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                fib[r] = (unsigned)((u * R + r) * 128 + 32 * q + lane);
+                alpha[r] = __ldg(g.alpha + fib[r]);
+            }
+            for (int t = 0; t < n_tiles; ++t, ++tile) {
+                const int cb = (int)(tile & 1);
+                if (!W.wait(acc_full + cb, (uint32_t)((tile >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+#pragma unroll
+                    for (int ch = 0; ch < N / 32; ++ch) {
+                        float v[32], mx;
+                        tmem_ld_red32(tmem + ((uint32_t)(32 * q) << 16) +
+                                          (uint32_t)(cb * C::ACC_COLS + r * N + ch * 32),
+                                      v, mx);
+                        tmem_wait_ld();
+                        const bool any = mx >= alpha[r];
+                        if (__any_sync(0xffffffffu, any)) {
+                            const unsigned col0 = (unsigned)(t * N + ch * 32);
+                            const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                const bool p = v[i] >= alpha[r] && col0 + i < (unsigned)cols;
+                                const unsigned m = __ballot_sync(0xffffffffu, p);
+                                if (m) {
+                                    if (scnt + 32 > STAGE_CAP) {
+                                        __syncwarp();
+                                        flush_stage(st, scnt, g, lane);
+                                    }
+                                    if (p) st[scnt + __popc(m & lt)] = make_uint2(fib[r], col0 + i);
+                                    scnt += __popc(m);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + cb);
+            }
+        }
+        __syncwarp();
+        flush_stage(st, scnt, g, lane);
+    }
+    // drain: make sure no TMA copy is still landing in this CTA's shared memory
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// ---- exact test of the survivors, overflow rescan, finalize ------------------------------------
+
+__device__ inline unsigned long long pack_key(float d2, int s, int o) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | ((unsigned long long)s << 1) |
+           (unsigned)o;
+}
+
+// Exact d^2 in orientation O with progressive discarding (Section 2.3 order: centre, ends,
+// four intermediate points, the rest); false as soon as a partial maximum exceeds bound2.
+template <int O>
+__device__ inline bool exact_one(const float* a, const float* b, float bound2, float& d2) {
+    constexpr int L = NPTS - 1;
+    float m = pd2(a, CENTRE, b, CENTRE);
+    if (!(m <= bound2)) return false;
+    m = fmaxf(m, fmaxf(pd2(a, 0, b, O ? L : 0), pd2(a, L, b, O ? 0 : L)));
+    if (!(m <= bound2)) return false;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        const int i = test3_point(qq);
+        m = fmaxf(m, pd2(a, i, b, O ? L - i : i));
+    }
+    if (!(m <= bound2)) return false;
+#pragma unroll
+    for (int i = 1; i < L; ++i)
+        if (!is_early_point(i)) m = fmaxf(m, pd2(a, i, b, O ? L - i : i));
+    if (!(m <= bound2)) return false;
+    d2 = m;
+    return true;
+}
+
+__global__ void k_exact_survivors(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
+    const long long cnt = min((long long)*g.cnt, g.cap);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < cnt;
+         e += (long long)gridDim.x * blockDim.x) {
+        const uint2 v = g.list[e];
+        const long long f = v.x;
+        const int s = (int)(v.y >> 1), o = (int)(v.y & 1u);
+        float a[NC];
+        const float* src = fib + f * NC;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) a[k] = __ldg(src + k);
+        float b[CROW];
+        const float4* b4 = reinterpret_cast<const float4*>(at.cen + (size_t)s * CROW);
+#pragma unroll
+        for (int k = 0; k < CROW / 4; ++k) {
+            const float4 t = __ldg(b4 + k);
+            b[4 * k] = t.x;
+            b[4 * k + 1] = t.y;
+            b[4 * k + 2] = t.z;
+            b[4 * k + 3] = t.w;
+        }
+        const float bound = fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
+        float d2;
+        const bool pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
+        if (pass) atomicMin(g.key + f, pack_key(d2, s, o));
+    }
+}
+
+// Fibers whose survivors did not fit the list: exact scan against the whole atlas.
+__global__ void k_overflow_rescan(const float* __restrict__ fib, long long n, AtlasView at,
+                                  GemmScratch g) {
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n || g.flag[f] == 0) return;
+    float a[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) a[k] = __ldg(fib + f * NC + k);
+    for (int s = 0; s < at.M; ++s) {
+        const float bound = fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
+        float d2;
+        int o;
+        if (exact_pair(a, at.cen + (size_t)s * CROW, bound, d2, o))
+            atomicMin(g.key + f, pack_key(d2, s, o));
+    }
+}
+
+__global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __restrict__ labels,
+                           float* __restrict__ dist, int* __restrict__ cidx,
+                           unsigned char* __restrict__ orient, long long pairs,
+                           long long* __restrict__ stats) {
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f == 0 && stats) {
+        stats[0] = pairs;
+        stats[1] = (long long)g.cnt[0];
+        stats[2] = (long long)g.cnt[1];
+    }
+    if (f >= n) return;
+    const unsigned long long k = g.key[f];
+    if (k == NAN_KEY || k == ~0ull) {
+        labels[f] = -1;
+        if (dist) dist[f] = k == NAN_KEY ? NAN : INFINITY;
+        if (cidx) cidx[f] = -1;
+        if (orient) orient[f] = 0;
+        return;
+    }
+    const int s = (int)((k & 0xffffffffull) >> 1);
+    labels[f] = at.bundle[s];
+    if (dist) dist[f] = sqrtf(__uint_as_float((unsigned)(k >> 32)));
+    if (cidx) cidx[f] = at.perm[s];
+    if (orient) orient[f] = (unsigned char)(k & 1ull);
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// rows x 64 operand, K-major, 128-byte swizzle, box of box_rows rows and 128 bytes of K.
+bool make_tmap(CUtensorMap* m, const void* ptr, long long rows, int fmt, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int elem = fmt == 1 ? 2 : 4;
+    cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(64 * elem)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_TFLOAT32, 2,
+              const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct GemmShape {
+    int fmt, R, N, S, ABUF;
+};
+
+// Tile shapes per operand format; entry 0 is the default.
+const GemmShape kBf16Shapes[] = {{1, 4, 64, 6, 2}, {1, 2, 128, 4, 2}, {1, 1, 256, 3, 2}};
+const GemmShape kTf32Shapes[] = {{2, 2, 128, 2, 1}, {2, 4, 64, 4, 1}, {2, 1, 256, 2, 2}};
+constexpr int kNumShapes = 3;
+
+template <int FMT, int R, int N, int S, int ABUF>
+cudaError_t launch_screen(const CUtensorMap& ta, const CUtensorMap& tb, long long n_units,
+                          int n_tiles, int cols, const GemmScratch& g, unsigned* status, int sms,
+                          cudaStream_t st) {
+    using C = GemmCfg<FMT, R, N, S, ABUF>;
+    auto kern = k_gemm_screen<FMT, R, N, S, ABUF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e) return e;
+    const long long grid = n_units < sms ? n_units : sms;
+    kern<<<(unsigned)grid, GEMM_THREADS, C::SMEM, st>>>(ta, tb, n_units, n_tiles, cols, g, status);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_screen(const GemmShape& sh, const CUtensorMap& ta, const CUtensorMap& tb,
+                            long long n_units, int n_tiles, int cols, const GemmScratch& g,
+                            unsigned* status, int sms, cudaStream_t st) {
+#define SEG_SHAPE(F, R_, N_, S_, AB)                                                      \
+    if (sh.fmt == F && sh.R == R_ && sh.N == N_ && sh.S == S_ && sh.ABUF == AB)          \
+        return launch_screen<F, R_, N_, S_, AB>(ta, tb, n_units, n_tiles, cols, g, status, \
+                                                sms, st);
+    SEG_SHAPE(1, 4, 64, 6, 2)
+    SEG_SHAPE(1, 2, 128, 4, 2)
+    SEG_SHAPE(1, 1, 256, 3, 2)
+    SEG_SHAPE(2, 2, 128, 2, 1)
+    SEG_SHAPE(2, 4, 64, 4, 1)
+    SEG_SHAPE(2, 1, 256, 2, 2)
+#undef SEG_SHAPE
+    return cudaErrorInvalidValue;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+int gemm_num_configs() { return kNumShapes; }
+
+seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->stats, 3 * sizeof(long long))) ||
+        (e = cudaMemsetAsync(g->stats, 0, 3 * sizeof(long long), st)))
+        return cuda_fail(e, "gemm stats");
+    g->cols = 2 * at.M;
+    g->cols_pad = (g->cols + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
+    if ((e = cudaMalloc(&g->b_bf16, (size_t)g->cols_pad * 64 * 2)) ||
+        (e = cudaMalloc(&g->b_tf32, (size_t)g->cols_pad * 64 * 4)))
+        return cuda_fail(e, "gemm operands");
+    const int threads = 128, blocks = (g->cols_pad + threads - 1) / threads;
+    k_prep_b<<<blocks, threads, 0, st>>>(at, 1, g->cols, g->cols_pad, g->b_bf16);
+    k_prep_b<<<blocks, threads, 0, st>>>(at, 2, g->cols, g->cols_pad, g->b_tf32);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "gemm operand prep");
+    return SEG_OK;
+}
 
 void free_gemm_atlas(GemmAtlas* g) {
     cudaFree(g->b_bf16);
@@ -20,9 +631,77 @@ void free_gemm_atlas(GemmAtlas* g) {
     *g = GemmAtlas{};
 }
 
-seg_status label_gemm(const AtlasView&, GemmAtlas*, ScratchArena*, std::mutex*, const float*,
-                      long long, bool, int*, float*, int*, unsigned char*, cudaStream_t) {
-    return fail(SEG_ERR_UNSUPPORTED, "seg_label: GEMM modes are not built yet");
+seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, std::mutex* mu,
+                      const float* fib, long long n, bool tf32, int* labels, float* dist,
+                      int* cidx, unsigned char* orient, cudaStream_t st, int config) {
+    const int fmt = tf32 ? 2 : 1;
+    if (config < 0 || config >= kNumShapes) config = 0;
+    const GemmShape sh = tf32 ? kTf32Shapes[config] : kBf16Shapes[config];
+    const long long rows_per_unit = 128LL * sh.R;
+    const long long n_units = (n + rows_per_unit - 1) / rows_per_unit;
+    const long long n_pad = n_units * rows_per_unit;
+    const int n_tiles = ga->cols_pad / sh.N;
+    if (n_pad >= (1LL << 32))
+        return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
+    // survivors: about 16 per fiber on atlases shaped like the paper's; 40 per fiber + slack
+    const long long cap = n * 40 + (1 << 20);
+    const size_t elem = tf32 ? 4 : 2;
+    const size_t off_alpha = align256((size_t)n_pad * 64 * elem);
+    const size_t off_key = off_alpha + align256((size_t)n_pad * 4);
+    const size_t off_flag = off_key + align256((size_t)n * 8);
+    const size_t off_cnt = off_flag + align256((size_t)n);
+    const size_t off_list = off_cnt + 256;
+    const size_t bytes = off_list + (size_t)cap * 8;
+
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    std::lock_guard<std::mutex> lock(*mu);
+    void* base = nullptr;
+    seg_status s = scratch_acquire(scratch, bytes, st, &base);
+    if (s != SEG_OK) return s;
+    unsigned char* b8 = static_cast<unsigned char*>(base);
+    GemmScratch g;
+    g.a = b8;
+    g.alpha = reinterpret_cast<float*>(b8 + off_alpha);
+    g.key = reinterpret_cast<unsigned long long*>(b8 + off_key);
+    g.flag = b8 + off_flag;
+    g.cnt = reinterpret_cast<unsigned long long*>(b8 + off_cnt);
+    g.list = reinterpret_cast<uint2*>(b8 + off_list);
+    g.cap = cap;
+
+    cudaError_t e = cudaSuccess;
+    CUtensorMap ta, tb;
+    if (!make_tmap(&ta, g.a, n_pad, fmt, 128) ||
+        !make_tmap(&tb, tf32 ? ga->b_tf32 : ga->b_bf16, ga->cols_pad, fmt, sh.N)) {
+        scratch_release(scratch, st);
+        return fail(SEG_ERR_CUDA, "seg_label: cuTensorMapEncodeTiled failed");
+    }
+    if (!e) e = cudaMemsetAsync(g.cnt, 0, 256, st);
+    if (!e) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
+    if (!e) {
+        k_prep_a<<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(fib, n, n_pad, at, fmt, g.a,
+                                                                   g.alpha, g.key);
+        e = cudaGetLastError();
+    }
+    if (!e) e = dispatch_screen(sh, ta, tb, n_units, n_tiles, ga->cols, g, at.status, sms, st);
+    if (!e) {
+        k_exact_survivors<<<sms * 8, 256, 0, st>>>(fib, at, g);
+        e = cudaGetLastError();
+    }
+    if (!e) {
+        k_overflow_rescan<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fib, n, at, g);
+        e = cudaGetLastError();
+    }
+    if (!e) {
+        k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            n, at, g, labels, dist, cidx, orient, n * (long long)ga->cols, ga->stats);
+        e = cudaGetLastError();
+    }
+    seg_status r = scratch_release(scratch, st);
+    if (e) return cuda_fail(e, "seg_label: GEMM mode");
+    return r;
 }
 
 }  // namespace seg

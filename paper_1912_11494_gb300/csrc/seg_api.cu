@@ -265,7 +265,8 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
     }
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
     return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n,
-                      mode == SEG_MODE_GEMM_TF32, d_labels, d_dist, d_cidx, d_orient, st);
+                      mode == SEG_MODE_GEMM_TF32, d_labels, d_dist, d_cidx, d_orient, st,
+                      a->config[(int)mode]);
 }
 
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,

@@ -38,7 +38,7 @@ void free_gemm_atlas(GemmAtlas* g);
 int gemm_num_configs();
 seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,
                       const float* fib, long long n, bool tf32, int* labels, float* dist,
-                      int* cidx, unsigned char* orient, cudaStream_t st);
+                      int* cidx, unsigned char* orient, cudaStream_t st, int config);
 
 // Cached CUDA graph of the batched launch.
 struct BatchState {

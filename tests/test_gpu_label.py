@@ -8,7 +8,7 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["plain"]
+MODES = ["plain", "gemm_bf16", "gemm_tf32"]
 
 
 @pytest.fixture(scope="module")
@@ -120,11 +120,16 @@ def test_invalid_atlas_rejected(dev):
         make_atlas(cen, a.bundle_of, a.thresholds, dev)
 
 
+@pytest.fixture(scope="module")
+def full_size():
+    return synth.workload("subject4145k_atlas10k", device="cuda")
+
+
 @pytest.mark.parametrize("mode", MODES)
-def test_full_size_sampled_parity(dev, mode):
+def test_full_size_sampled_parity(dev, mode, full_size):
     """4,145,000 fibers x 10,000 centroids labelled in one call (the benchmark's launch);
-    3,000 sampled fibers are checked one by one against the oracle."""
-    atlas_np, fib = synth.workload("subject4145k_atlas10k", device="cuda")
+    3,000 sampled fibers and the ragged tail are checked one by one against the oracle."""
+    atlas_np, fib = full_size
     at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
     lab, dist, cidx, orient = run(at, fib, dev, mode)
     rng = np.random.default_rng(123)
@@ -135,6 +140,22 @@ def test_full_size_sampled_parity(dev, mode):
     assert res["labelled"] > 0.6 * len(idx)
     frac = (lab >= 0).mean()
     assert 0.6 < frac < 0.9
+
+
+@pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_tf32"])
+def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
+    """The prune is conservative and survivors go through the same FP32 exact test, so the GEMM
+    modes reproduce the plain kernel bit for bit on every fiber, not only the decidable ones."""
+    for atlas_np, fib in (small_workload, full_size):
+        at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+        ref = run(at, fib, dev, "plain")
+        got = run(at, fib, dev, mode)
+        for x, y in zip(ref, got):
+            np.testing.assert_array_equal(x, y)
+        st = binding.seg_gemm_stats(at)
+        assert st["pairs"] == len(fib) * 2 * atlas_np.M
+        assert 0 < st["survivors"] < 0.01 * st["pairs"]
+        assert st["overflow_fibers"] == 0
 
 
 def test_every_tile_shape_identical(dev, small_workload):
