@@ -39,9 +39,10 @@
 namespace seg {
 namespace {
 
-constexpr int GEMM_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int EPI_WARPS = 8;       // two epilogue warps per TMEM lane quarter
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA, then epilogue
 constexpr int COL_ALIGN = 256;     // columns padded to a multiple of this
-constexpr int STAGE_CAP = 256;     // survivors staged per epilogue warp
+constexpr int STAGE_CAP = 128;     // survivor records staged per epilogue warp
 constexpr unsigned long long NAN_KEY = ~0ull - 1ull;
 constexpr float PAD_NEG = -1e30f;  // pad of padding columns: never survives
 
@@ -57,13 +58,15 @@ __host__ __device__ inline double kappa_of(int fmt) {
     return 1.05 * (2.0 * u + u * u) + 2.0 * GAMMA_ACC;
 }
 
+// A survivor record: fiber, first column of a 32-column chunk, and the mask of its columns
+// that survived (one record per fiber per chunk with survivors).
 struct GemmScratch {
     void* a;                      // fiber operand [n_pad][64]
     float* alpha;                 // [n_pad]
     unsigned long long* key;      // [n]
     unsigned char* flag;          // [n] survivors dropped for lack of list space
-    uint2* list;                  // [cap] (fiber, column)
-    unsigned long long* cnt;      // [0] survivors appended, [1] fibers flagged
+    uint4* list;                  // [cap] records {fiber, col0, mask, 0}
+    unsigned long long* cnt;      // [0] records appended, [1] fibers flagged, [2] survivors
     long long cap;
 };
 
@@ -122,45 +125,72 @@ __global__ void k_prep_b(AtlasView at, int fmt, int cols, int cols_pad, void* ou
     }
 }
 
-// Fiber rows: centred coordinates, 1 in the pad column, alpha_i; keys initialised.
-__global__ void k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView at,
-                         int fmt, void* __restrict__ out, float* __restrict__ alpha,
-                         unsigned long long* __restrict__ key) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
+// Fiber rows: centred coordinates, 1 in the pad column, alpha_i; keys initialised. One warp
+// per 32 rows: the 32 x 63 input floats are read with coalesced loads into shared memory, each
+// lane converts one row, and the 32 output rows go back out with coalesced stores.
+constexpr int PREP_WARPS = 2;
+
+__global__ void __launch_bounds__(PREP_WARPS * 32)
+k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView at, int fmt,
+         void* __restrict__ out, float* __restrict__ alpha, unsigned long long* __restrict__ key) {
+    __shared__ float s_in[PREP_WARPS][32 * NC];
+    __shared__ uint32_t s_out[PREP_WARPS][32 * 65];  // 32 rows of up to 64 words, padded
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long r0 = ((long long)blockIdx.x * PREP_WARPS + w) * 32;
+    if (r0 >= n_pad) return;
+    const long long rows_in = max(0LL, min(32LL, n - r0));
+    float* si = s_in[w];
+    const float* src = fib + r0 * NC;
+    for (int k = lane; k < rows_in * NC; k += 32) si[k] = __ldg(src + k);
+    __syncwarp();
+    const long long i = r0 + lane;
     float p[NC];
-    bool finite = i < n;
+    bool finite = lane < rows_in;
     double n2 = 0.0;
-    if (i < n) {
-        const float* a = fib + i * NC;
-        for (int k = 0; k < NC; ++k) finite = finite && isfinite(__ldg(a + k));
+    if (finite) {
+#pragma unroll
         for (int t = 0; t < NPTS; ++t) {
-            p[3 * t] = __ldg(a + 3 * t) - at.c0x;
-            p[3 * t + 1] = __ldg(a + 3 * t + 1) - at.c0y;
-            p[3 * t + 2] = __ldg(a + 3 * t + 2) - at.c0z;
+            p[3 * t] = si[lane * NC + 3 * t] - at.c0x;
+            p[3 * t + 1] = si[lane * NC + 3 * t + 1] - at.c0y;
+            p[3 * t + 2] = si[lane * NC + 3 * t + 2] - at.c0z;
         }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) finite = finite && isfinite(p[k]);
     }
     if (!finite) {
+#pragma unroll
         for (int k = 0; k < NC; ++k) p[k] = 0.0f;
     } else {
+#pragma unroll
         for (int k = 0; k < NC; ++k) n2 += (double)p[k] * p[k];
     }
     const double kap = kappa_of(fmt);
     const double al = 0.5 * (1.0 - kap) * n2 - (1e-5 * n2 + 0.005);
     alpha[i] = finite ? __double2float_rd(al) : INFINITY;
-    if (i < n) key[i] = finite ? ~0ull : NAN_KEY;
-    if (fmt == 1) {
-        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(
-            reinterpret_cast<__nv_bfloat16*>(out) + (size_t)i * 64);
-        for (int k = 0; k < 31; ++k) o[k] = __floats2bfloat162_rn(p[2 * k], p[2 * k + 1]);
-        o[31] = __floats2bfloat162_rn(p[62], 1.0f);
-    } else {
-        float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + (size_t)i * 64);
-        for (int k = 0; k < 15; ++k)
-            o[k] = make_float4(tf32_rn(p[4 * k]), tf32_rn(p[4 * k + 1]), tf32_rn(p[4 * k + 2]),
-                               tf32_rn(p[4 * k + 3]));
-        o[15] = make_float4(tf32_rn(p[60]), tf32_rn(p[61]), tf32_rn(p[62]), 1.0f);
+    if (i < n) {
+        bool fin_in = true;  // non-finite input (not only padding) gets the NaN key
+        for (int k = 0; k < NC; ++k) fin_in = fin_in && isfinite(si[lane * NC + k]);
+        key[i] = fin_in ? ~0ull : NAN_KEY;
     }
+    uint32_t* so = s_out[w];
+    const int words = fmt == 1 ? 32 : 64;  // 32-bit words per output row
+    if (fmt == 1) {
+#pragma unroll
+        for (int k = 0; k < 31; ++k) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(p[2 * k], p[2 * k + 1]);
+            so[lane * 33 + k] = *reinterpret_cast<uint32_t*>(&b);
+        }
+        __nv_bfloat162 b = __floats2bfloat162_rn(p[62], 1.0f);
+        so[lane * 33 + 31] = *reinterpret_cast<uint32_t*>(&b);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 63; ++k) so[lane * 65 + k] = __float_as_uint(tf32_rn(p[k]));
+        so[lane * 65 + 63] = __float_as_uint(1.0f);
+    }
+    __syncwarp();
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out) + r0 * words;
+    const int stride = fmt == 1 ? 33 : 65;
+    for (int k = lane; k < 32 * words; k += 32) dst[k] = so[(k / words) * stride + (k % words)];
 }
 
 // ---- the tensor-core screen ------------------------------------------------------------------
@@ -178,7 +208,7 @@ struct GemmCfg {
     static constexpr int A_OFF = 0;
     static constexpr int B_OFF = A_OFF + ABUF * R * A_TILE;
     static constexpr int ST_OFF = B_OFF + S * B_TILE;         // survivor staging
-    static constexpr int BAR_OFF = ST_OFF + 4 * STAGE_CAP * 8;
+    static constexpr int BAR_OFF = ST_OFF + EPI_WARPS * STAGE_CAP * 16;
     static constexpr int NBAR = 2 * ABUF + 2 * S + 5;
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16 + 1024;  // + alignment slack
     static_assert(2 * ACC_COLS <= 512, "two accumulators must fit TMEM");
@@ -193,26 +223,35 @@ struct Waiter {
     // wait ran past its limit (then it starts the abort)
     __device__ bool wait(uint64_t* bar, uint32_t parity) const {
         if (mbar_try_wait(bar, parity)) return true;
-        const uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(bar, parity)) {
-            if (*abort) return false;
-            if (globaltimer_ns() - t0 > 2000000000ull) {
-                *abort = 1;
-                atomicOr(status, ST_TIMEOUT);
-                return false;
+        // poll; look at the abort flag and the clock only every 1024 polls, so a completed
+        // phase is seen without the latency of a timer read
+        uint64_t t0 = 0;
+        for (uint32_t i = 0;; ++i) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if ((i & 1023u) == 0u) {
+                if (*abort) return false;
+                const uint64_t now = globaltimer_ns();
+                if (i == 0) {
+                    t0 = now;
+                } else if (now - t0 > 2000000000ull) {
+                    *abort = 1;
+                    atomicOr(status, ST_TIMEOUT);
+                    return false;
+                }
             }
         }
-        return true;
     }
 };
 
-__device__ inline void flush_stage(uint2* st, int& scnt, const GemmScratch& g, int lane) {
+__device__ inline void flush_stage(uint4* st, int& scnt, const GemmScratch& g, int lane) {
     if (scnt == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(g.cnt, (unsigned long long)scnt);
     base = __shfl_sync(0xffffffffu, base, 0);
+    unsigned surv = 0;
     for (int i = lane; i < scnt; i += 32) {
-        const uint2 e = st[i];
+        const uint4 e = st[i];
+        surv += __popc(e.z);
         if ((long long)(base + i) < g.cap) {
             g.list[base + i] = e;
         } else if (g.flag[e.x] == 0) {
@@ -220,6 +259,9 @@ __device__ inline void flush_stage(uint2* st, int& scnt, const GemmScratch& g, i
             atomicAdd(g.cnt + 1, 1ull);
         }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+    if (lane == 0) atomicAdd(g.cnt + 2, (unsigned long long)surv);
     __syncwarp();
     scnt = 0;
 }
@@ -254,7 +296,7 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(acc_full + i, 1);
-            mbar_init(acc_empty + i, 4);
+            mbar_init(acc_empty + i, EPI_WARPS);
         }
         mbar_init(mma_done, 1);
         s_abort = 0;
@@ -368,19 +410,24 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         mbar_wait_bounded(mma_done, 0);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
-        uint2* st = reinterpret_cast<uint2*>(smem + C::ST_OFF) + (warp - 2) * STAGE_CAP;
+        // Warp w reads TMEM lane quarter w % 4 (the hardware's rule) and, with its partner
+        // warp of the same quarter, half of the 32-column chunks of each accumulator. Two
+        // tcgen05.ld.red are in flight per wait.
+        constexpr int CPR = N / 32;               // chunks per fiber tile row block
+        constexpr int CHUNKS = R * CPR;           // chunks per accumulator
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        uint4* st = reinterpret_cast<uint4*>(smem + C::ST_OFF) + (warp - 2) * STAGE_CAP;
         int scnt = 0;
         long long tile = 0;
         bool ok = true;
+        const unsigned lt = (1u << lane) - 1u;
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            float alpha[R];
-            unsigned fib[R];
+            float al[4];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                fib[r] = (unsigned)((u * R + r) * 128 + 32 * q + lane);
-                alpha[r] = __ldg(g.alpha + fib[r]);
-            }
+            for (int r = 0; r < 4; ++r)
+                al[r] = r < R ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane) : INFINITY;
+            const unsigned fib0 = (unsigned)(u * R * 128 + 32 * q + lane);
             for (int t = 0; t < n_tiles; ++t, ++tile) {
                 const int cb = (int)(tile & 1);
                 if (!W.wait(acc_full + cb, (uint32_t)((tile >> 1) & 1))) {
@@ -388,33 +435,37 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     break;
                 }
                 tc_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cb * C::ACC_COLS);
+#pragma unroll 1
+                for (int c0 = half; c0 < CHUNKS; c0 += 4) {
+                    float v[2][32], mx[2];
+                    tmem_ld_red32(tbase + (uint32_t)(32 * c0), v[0], mx[0]);
+                    const bool two = c0 + 2 < CHUNKS;
+                    if (two) tmem_ld_red32(tbase + (uint32_t)(32 * (c0 + 2)), v[1], mx[1]);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1 && !two) break;
+                        const int c = c0 + 2 * h;
+                        const int r = c / CPR;
+                        const float a = r == 0 ? al[0] : r == 1 ? al[1] : r == 2 ? al[2] : al[3];
+                        if (!__any_sync(0xffffffffu, mx[h] >= a)) continue;
+                        // rare: this lane's surviving columns of the chunk as a bit mask,
+                        // appended as one record (warp-aggregated)
+                        const unsigned col0 = (unsigned)(t * N + (c % CPR) * 32);
+                        unsigned mask = 0;
 #pragma unroll
-                    for (int ch = 0; ch < N / 32; ++ch) {
-                        float v[32], mx;
-                        tmem_ld_red32(tmem + ((uint32_t)(32 * q) << 16) +
-                                          (uint32_t)(cb * C::ACC_COLS + r * N + ch * 32),
-                                      v, mx);
-                        tmem_wait_ld();
-                        const bool any = mx >= alpha[r];
-                        if (__any_sync(0xffffffffu, any)) {
-                            const unsigned col0 = (unsigned)(t * N + ch * 32);
-                            const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                const bool p = v[i] >= alpha[r] && col0 + i < (unsigned)cols;
-                                const unsigned m = __ballot_sync(0xffffffffu, p);
-                                if (m) {
-                                    if (scnt + 32 > STAGE_CAP) {
-                                        __syncwarp();
-                                        flush_stage(st, scnt, g, lane);
-                                    }
-                                    if (p) st[scnt + __popc(m & lt)] = make_uint2(fib[r], col0 + i);
-                                    scnt += __popc(m);
-                                }
-                            }
-                        }
+                        for (int i = 0; i < 32; ++i) mask |= (v[h][i] >= a ? 1u : 0u) << i;
+                        if (col0 + 32 > (unsigned)cols)
+                            mask &= col0 >= (unsigned)cols ? 0u : (1u << (cols - col0)) - 1u;
+                        if (scnt + 32 > STAGE_CAP) flush_stage(st, scnt, g, lane);
+                        const bool p = mask != 0u;
+                        const unsigned m = __ballot_sync(0xffffffffu, p);
+                        if (p)
+                            st[scnt + __popc(m & lt)] =
+                                make_uint4(fib0 + (unsigned)(r * 128), col0, mask, 0u);
+                        scnt += __popc(m);
+                        __syncwarp();
                     }
                 }
                 tc_fence_before();
@@ -461,31 +512,31 @@ __device__ inline bool exact_one(const float* a, const float* b, float bound2, f
     return true;
 }
 
+// One thread per survivor record: the fiber is loaded once, then each surviving column of the
+// record (centroid s = column / 2, orientation = column % 2) runs the exact test.
 __global__ void k_exact_survivors(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
     const long long cnt = min((long long)*g.cnt, g.cap);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < cnt;
          e += (long long)gridDim.x * blockDim.x) {
-        const uint2 v = g.list[e];
-        const long long f = v.x;
-        const int s = (int)(v.y >> 1), o = (int)(v.y & 1u);
+        const uint4 rec = g.list[e];
+        const long long f = rec.x;
         float a[NC];
         const float* src = fib + f * NC;
 #pragma unroll
         for (int k = 0; k < NC; ++k) a[k] = __ldg(src + k);
-        float b[CROW];
-        const float4* b4 = reinterpret_cast<const float4*>(at.cen + (size_t)s * CROW);
-#pragma unroll
-        for (int k = 0; k < CROW / 4; ++k) {
-            const float4 t = __ldg(b4 + k);
-            b[4 * k] = t.x;
-            b[4 * k + 1] = t.y;
-            b[4 * k + 2] = t.z;
-            b[4 * k + 3] = t.w;
+        unsigned mask = rec.z;
+        while (mask) {
+            const int bit = __ffs((int)mask) - 1;
+            mask &= mask - 1u;
+            const unsigned col = rec.y + (unsigned)bit;
+            const int s = (int)(col >> 1), o = (int)(col & 1u);
+            const float* b = at.cen + (size_t)s * CROW;  // read point by point (L1-resident)
+            const float bound =
+                fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
+            float d2;
+            const bool pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
+            if (pass) atomicMin(g.key + f, pack_key(d2, s, o));
         }
-        const float bound = fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
-        float d2;
-        const bool pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
-        if (pass) atomicMin(g.key + f, pack_key(d2, s, o));
     }
 }
 
@@ -513,7 +564,7 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __rest
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f == 0 && stats) {
         stats[0] = pairs;
-        stats[1] = (long long)g.cnt[0];
+        stats[1] = (long long)g.cnt[2];
         stats[2] = (long long)g.cnt[1];
     }
     if (f >= n) return;
@@ -643,15 +694,16 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const int n_tiles = ga->cols_pad / sh.N;
     if (n_pad >= (1LL << 32))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
-    // survivors: about 16 per fiber on atlases shaped like the paper's; 40 per fiber + slack
-    const long long cap = n * 40 + (1 << 20);
+    // survivor records (one per fiber per 32-column chunk with survivors): about 1.6 per fiber
+    // on atlases shaped like the paper's; room for 8 per fiber + slack
+    const long long cap = n * 8 + (1 << 20);
     const size_t elem = tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * 64 * elem);
     const size_t off_key = off_alpha + align256((size_t)n_pad * 4);
     const size_t off_flag = off_key + align256((size_t)n * 8);
     const size_t off_cnt = off_flag + align256((size_t)n);
     const size_t off_list = off_cnt + 256;
-    const size_t bytes = off_list + (size_t)cap * 8;
+    const size_t bytes = off_list + (size_t)cap * 16;
 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -668,7 +720,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     g.key = reinterpret_cast<unsigned long long*>(b8 + off_key);
     g.flag = b8 + off_flag;
     g.cnt = reinterpret_cast<unsigned long long*>(b8 + off_cnt);
-    g.list = reinterpret_cast<uint2*>(b8 + off_list);
+    g.list = reinterpret_cast<uint4*>(b8 + off_list);
     g.cap = cap;
 
     cudaError_t e = cudaSuccess;
@@ -681,8 +733,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) e = cudaMemsetAsync(g.cnt, 0, 256, st);
     if (!e) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
     if (!e) {
-        k_prep_a<<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(fib, n, n_pad, at, fmt, g.a,
-                                                                   g.alpha, g.key);
+        const long long rows_per_block = 32LL * PREP_WARPS;
+        k_prep_a<<<(unsigned)((n_pad + rows_per_block - 1) / rows_per_block), PREP_WARPS * 32, 0,
+                   st>>>(fib, n, n_pad, at, fmt, g.a, g.alpha, g.key);
         e = cudaGetLastError();
     }
     if (!e) e = dispatch_screen(sh, ta, tb, n_units, n_tiles, ga->cols, g, at.status, sms, st);

@@ -45,15 +45,22 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// Wait for the mbarrier phase with a wall-clock limit. Returns false on timeout.
+// Wait for the mbarrier phase with a wall-clock limit (the clock is read every 1024 polls).
+// Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer_ns() - t0 > limit_ns) return false;
+    uint64_t t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 0u) {
+            const uint64_t now = globaltimer_ns();
+            if (i == 0)
+                t0 = now;
+            else if (now - t0 > limit_ns)
+                return false;
+        }
     }
-    return true;
 }
 
 // 1D bulk copy global -> shared (TMA engine), completion on `bar` (transaction bytes).
