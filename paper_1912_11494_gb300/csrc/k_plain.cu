@@ -97,33 +97,29 @@ __device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float
     }
 }
 
+// Label the TW fibers starting at f0 of one subject; the calling warp owns the tile and the
+// slice ws of shared memory (its mbarrier initialised; `phase` = tiles this warp did before).
 template <int PC, int PK>
-__global__ void __launch_bounds__(PW * 32)
-k_label_plain(const float* __restrict__ fib, long long n, AtlasView at, int fib_aligned,
-              int* __restrict__ labels, float* __restrict__ dist, int* __restrict__ cidx,
-              unsigned char* __restrict__ orient) {
+__device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long long n,
+                                           long long f0, const AtlasView& at, int fib_aligned,
+                                           int* __restrict__ labels, float* __restrict__ dist,
+                                           int* __restrict__ cidx,
+                                           unsigned char* __restrict__ orient,
+                                           unsigned char* ws, uint32_t phase) {
     using WS = WarpSmem<PC, PK>;
     constexpr int CH = 32 * PC;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* ws = smem + warp * WS::bytes;
+    const int lane = threadIdx.x & 31;
     float* fc = reinterpret_cast<float*>(ws + WS::fc_off);
     float4* fs = reinterpret_cast<float4*>(ws + WS::fs_off);
     unsigned long long* key = reinterpret_cast<unsigned long long*>(ws + WS::key_off);
     unsigned* q = reinterpret_cast<unsigned*>(ws + WS::q_off);
     uint64_t* bar = reinterpret_cast<uint64_t*>(ws + WS::bar_off);
-
-    const long long f0 = ((long long)blockIdx.x * PW + warp) * TW;
-    if (f0 >= n) return;  // warp-uniform
     const int nf = (int)min((long long)TW, n - f0);
     const bool tma_tile = fib_aligned && nf == TW;
-    if (lane == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
     __syncwarp();
     if (tma_tile) {
         if (lane == 0) {
+            fence_proxy_async_smem();  // earlier tiles' reads of this slice precede the copy
             mbar_arrive_expect_tx(bar, (uint32_t)(TW * NC * 4));
             bulk_g2s(fc, fib + f0 * NC, (uint32_t)(TW * NC * 4), bar);
         }
@@ -137,13 +133,13 @@ k_label_plain(const float* __restrict__ fib, long long n, AtlasView at, int fib_
     for (int c = 0; c < PC; ++c) nxt[c] = __ldg(at.scr2 + c * 32 + lane);
     (void)WS::QW;
     int ok = 1;
-    if (tma_tile && lane == 0) ok = (int)mbar_wait_bounded(bar, 0);
+    if (tma_tile && lane == 0) ok = (int)mbar_wait_bounded(bar, phase & 1u);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     if (!ok) {
         if (lane == 0) {
             atomicOr(at.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(bar, phase & 1u);
         }
         return;
     }
@@ -292,6 +288,58 @@ k_label_plain(const float* __restrict__ fib, long long n, AtlasView at, int fib_
     }
 }
 
+template <int PC, int PK>
+__global__ void __launch_bounds__(PW * 32)
+k_label_plain(const float* __restrict__ fib, long long n, AtlasView at, int fib_aligned,
+              int* __restrict__ labels, float* __restrict__ dist, int* __restrict__ cidx,
+              unsigned char* __restrict__ orient) {
+    using WS = WarpSmem<PC, PK>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* ws = smem + warp * WS::bytes;
+    const long long f0 = ((long long)blockIdx.x * PW + warp) * TW;
+    if (f0 >= n) return;  // warp-uniform
+    if (lane == 0) {
+        mbar_init(reinterpret_cast<uint64_t*>(ws + WS::bar_off), 1);
+        fence_mbar_init();
+    }
+    plain_tile<PC, PK>(fib, n, f0, at, fib_aligned, labels, dist, cidx, orient, ws, 0u);
+}
+
+// Many subjects in one persistent launch: every warp takes (subject, tile) work items from a
+// global counter until the table's tiles are exhausted (no warp ever waits for another).
+template <int PC, int PK>
+__global__ void __launch_bounds__(PW * 32)
+k_label_plain_batch(const BatchEntry* __restrict__ table, int nsubj,
+                    unsigned long long* __restrict__ counter, AtlasView at) {
+    using WS = WarpSmem<PC, PK>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* ws = smem + warp * WS::bytes;
+    if (lane == 0) {
+        mbar_init(reinterpret_cast<uint64_t*>(ws + WS::bar_off), 1);
+        fence_mbar_init();
+    }
+    const long long total = table[nsubj].tile0;
+    uint32_t done = 0;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((long long)t >= total) break;
+        int lo = 0, hi = nsubj - 1;  // last subject whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid].tile0 <= (long long)t) lo = mid; else hi = mid - 1;
+        }
+        const BatchEntry e = table[lo];
+        const long long f0 = ((long long)t - e.tile0) * TW;
+        plain_tile<PC, PK>(e.fib, e.n, f0, at, ((uintptr_t)e.fib % 16) == 0, e.labels, e.dist,
+                           nullptr, nullptr, ws, done);
+        if (((uintptr_t)e.fib % 16) == 0 && min((long long)TW, e.n - f0) == TW) ++done;
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -314,6 +362,22 @@ cudaError_t launch_cfg(const AtlasView& at, const float* fib, long long n, int* 
 
 }  // namespace
 
+template <int PC, int PK>
+cudaError_t launch_batch_cfg(const BatchEntry* table, int nsubj, unsigned long long* counter,
+                             const AtlasView& at, int sms, cudaStream_t st) {
+    const size_t smem = PW * WarpSmem<PC, PK>::bytes;
+    auto kern = k_label_plain_batch<PC, PK>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PW * 32, smem);
+    if (e) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<(unsigned)(sms * per_sm), PW * 32, smem, st>>>(table, nsubj, counter, at);
+    return cudaGetLastError();
+}
+
 // Tile shapes (centroids per lane, fibers per vote) the autotuner chooses from.
 // Entry 0 is the default (fastest measured on the 4,145,000 x 10,000 workload).
 const int kPlainConfigs[][2] = {{8, 4}, {4, 2}, {4, 4}, {8, 2}, {2, 8}, {4, 8}};
@@ -331,6 +395,19 @@ cudaError_t launch_label_plain(const AtlasView& at, const float* fib, long long 
         case 4: return launch_cfg<2, 8>(at, fib, n, labels, dist, cidx, orient, st);
         case 5: return launch_cfg<4, 8>(at, fib, n, labels, dist, cidx, orient, st);
         default: return launch_cfg<8, 4>(at, fib, n, labels, dist, cidx, orient, st);
+    }
+}
+
+cudaError_t launch_label_plain_batch(const BatchEntry* table, int nsubj,
+                                     unsigned long long* counter, const AtlasView& at, int sms,
+                                     cudaStream_t st, int config) {
+    switch (config) {
+        case 1: return launch_batch_cfg<4, 2>(table, nsubj, counter, at, sms, st);
+        case 2: return launch_batch_cfg<4, 4>(table, nsubj, counter, at, sms, st);
+        case 3: return launch_batch_cfg<8, 2>(table, nsubj, counter, at, sms, st);
+        case 4: return launch_batch_cfg<2, 8>(table, nsubj, counter, at, sms, st);
+        case 5: return launch_batch_cfg<4, 8>(table, nsubj, counter, at, sms, st);
+        default: return launch_batch_cfg<8, 4>(table, nsubj, counter, at, sms, st);
     }
 }
 

@@ -289,7 +289,7 @@ seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* c
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
     return batch_launch(a->view, &a->gemm, &a->batch, &a->scratch, &a->mu, nsubj, h_fibers,
                         reinterpret_cast<const long long*>(h_counts), (int)mode, h_labels,
-                        h_dist, (cudaStream_t)stream);
+                        h_dist, (cudaStream_t)stream, a->config[(int)mode]);
 }
 
 seg_status seg_apply_affine(const float* d_in, int64_t n, const double* h_affine12, float* d_out,

@@ -36,10 +36,24 @@ struct AtlasView {
     unsigned* status;           // device status word
 };
 
+// One subject of a batched call (device table; entry nsubj holds only tile0 = total tiles).
+struct BatchEntry {
+    const float* fib;
+    long long n;
+    int* labels;
+    float* dist;
+    long long tile0;  // first work item (32-fiber tile) of this subject
+    long long pad;
+};
+
 // Plain exact labelling of n fibers (SEG_MODE_PLAIN).
 cudaError_t launch_label_plain(const AtlasView& at, const float* fib, long long n, int* labels,
                                float* dist, int* cidx, unsigned char* orient, cudaStream_t st,
                                int config = 0);
+cudaError_t launch_label_plain_batch(const BatchEntry* table, int nsubj,
+                                     unsigned long long* counter, const AtlasView& at, int sms,
+                                     cudaStream_t st, int config);
+constexpr int PLAIN_TILE = 32;  // fibers per work item of the plain kernels
 extern const int kPlainConfigs[][2];
 extern const int kNumPlainConfigs;
 

@@ -40,20 +40,24 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, 
                       const float* fib, long long n, bool tf32, int* labels, float* dist,
                       int* cidx, unsigned char* orient, cudaStream_t st, int config);
 
-// Cached CUDA graph of the batched launch.
+// Cached CUDA graph of the batched launch: counter reset, work-table upload (from a pinned
+// host copy the host rewrites before each replay) and the persistent kernel.
 struct BatchState {
-    void* graph_exec = nullptr;  // cudaGraphExec_t
-    int nsubj = 0;
-    int mode = -1;
-    void* table = nullptr;        // device work table
-    size_t table_bytes = 0;
+    void* graph_exec = nullptr;   // cudaGraphExec_t
+    int nsubj = -1;
+    int config = -1;
+    void* table = nullptr;        // device BatchEntry[nsubj + 1]
+    void* table_host = nullptr;   // pinned host copy
+    size_t table_cap = 0;         // entries allocated
     void* counter = nullptr;      // device work counter
+    void* cap_stream = nullptr;   // cudaStream_t used for capture
+    void* done = nullptr;         // cudaEvent_t recorded after each replay
 };
 void free_batch(BatchState* b);
 seg_status batch_launch(const AtlasView& at, GemmAtlas* g, BatchState* b, ScratchArena* scratch,
                         std::mutex* mu, int nsubj, const float* const* fib,
                         const long long* counts, int mode, int* const* labels,
-                        float* const* dist, cudaStream_t st);
+                        float* const* dist, cudaStream_t st, int config);
 
 seg_status grad_launch(const AtlasView& at, const int* inv_perm, ScratchArena* scratch,
                        std::mutex* mu, const float* fib, long long n, const double* h_aff,
