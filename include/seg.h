@@ -178,6 +178,18 @@ seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config);
 seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config);
 
 /*
+ * Kernel timing (observability; not in the paper). While enabled on an atlas, every kernel the
+ * library launches for it records a pair of CUDA events on its stream (no host synchronisation).
+ * seg_profile_read waits for those events and returns, for one kernel name, the number of
+ * launches and their summed duration in milliseconds since profiling was (re)enabled.
+ * Kernel names: "plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
+ * "gemm_finalize", "grad". Enabling (or disabling) clears what was recorded.
+ */
+seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable);
+seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launches,
+                            double* total_ms);
+
+/*
  * Wait for `stream`, then report and clear the atlas's device status word: SEG_OK, or the first
  * device-side error (SEG_ERR_TIMEOUT, SEG_ERR_OVERFLOW) recorded since the last call.
  */

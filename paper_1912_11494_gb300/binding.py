@@ -41,6 +41,9 @@ SIGNATURES = [
     ("seg_get_config", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I32)]),
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    ("seg_profile_enable", ctypes.c_int, [_P, _I32]),
+    ("seg_profile_read", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64),
+                                        ctypes.POINTER(ctypes.c_double)]),
 ]
 
 _lib = None
@@ -231,3 +234,20 @@ def seg_gemm_stats(atlas: Atlas):
     p, s, o = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib().seg_gemm_stats(atlas.handle, ctypes.byref(p), ctypes.byref(s), ctypes.byref(o)))
     return dict(pairs=p.value, survivors=s.value, overflow_fibers=o.value)
+
+
+PROFILED_KERNELS = ("plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
+                    "gemm_finalize", "grad")
+
+
+def seg_profile_enable(atlas: Atlas, enable: bool = True):
+    _check(lib().seg_profile_enable(atlas.handle, 1 if enable else 0))
+
+
+def seg_profile_read(atlas: Atlas, kernel: str):
+    """(launches, total milliseconds) of one kernel since profiling was enabled."""
+    c = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(lib().seg_profile_read(atlas.handle, kernel.encode(), ctypes.byref(c),
+                                  ctypes.byref(ms)))
+    return c.value, ms.value

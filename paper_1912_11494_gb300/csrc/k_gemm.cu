@@ -684,7 +684,8 @@ void free_gemm_atlas(GemmAtlas* g) {
 
 seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, std::mutex* mu,
                       const float* fib, long long n, bool tf32, int* labels, float* dist,
-                      int* cidx, unsigned char* orient, cudaStream_t st, int config) {
+                      int* cidx, unsigned char* orient, cudaStream_t st, int config,
+                      Profiler* prof) {
     const int fmt = tf32 ? 2 : 1;
     if (config < 0 || config >= kNumShapes) config = 0;
     const GemmShape sh = tf32 ? kTf32Shapes[config] : kBf16Shapes[config];
@@ -733,21 +734,28 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) e = cudaMemsetAsync(g.cnt, 0, 256, st);
     if (!e) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
     if (!e) {
+        ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
         k_prep_a<<<(unsigned)((n_pad + rows_per_block - 1) / rows_per_block), PREP_WARPS * 32, 0,
                    st>>>(fib, n, n_pad, at, fmt, g.a, g.alpha, g.key);
         e = cudaGetLastError();
     }
-    if (!e) e = dispatch_screen(sh, ta, tb, n_units, n_tiles, ga->cols, g, at.status, sms, st);
     if (!e) {
+        ProfScope ps(prof, PROF_GEMM_SCREEN, st);
+        e = dispatch_screen(sh, ta, tb, n_units, n_tiles, ga->cols, g, at.status, sms, st);
+    }
+    if (!e) {
+        ProfScope ps(prof, PROF_GEMM_EXACT, st);
         k_exact_survivors<<<sms * 8, 256, 0, st>>>(fib, at, g);
         e = cudaGetLastError();
     }
     if (!e) {
+        ProfScope ps(prof, PROF_GEMM_RESCAN, st);
         k_overflow_rescan<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fib, n, at, g);
         e = cudaGetLastError();
     }
     if (!e) {
+        ProfScope ps(prof, PROF_GEMM_FINAL, st);
         k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
             n, at, g, labels, dist, cidx, orient, n * (long long)ga->cols, ga->stats);
         e = cudaGetLastError();

@@ -29,6 +29,34 @@ seg_status cuda_fail(cudaError_t e, const char* what) {
                 cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+void Profiler::begin(int slot, cudaStream_t st, cudaEvent_t* end_out) {
+    if (used == pool.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) || cudaEventCreate(&b)) {
+            if (a) cudaEventDestroy(a);
+            *end_out = nullptr;
+            return;
+        }
+        pool.emplace_back(a, b);
+    }
+    cudaEventRecord(pool[used].first, st);
+    *end_out = pool[used].second;
+    slot_of.push_back(slot);
+    ++used;
+}
+
+void Profiler::clear() {
+    used = 0;
+    slot_of.clear();
+}
+
+Profiler::~Profiler() {
+    for (auto& pr : pool) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+}
+
 namespace {
 
 // Sorted copy of the atlas: row s of the output is caller centroid perm[s].
@@ -97,6 +125,7 @@ struct seg_atlas {
     ScratchArena scratch{};
     BatchState batch{};
     int config[3] = {0, 0, 0};  // tile-shape selection per seg_mode
+    Profiler prof;
     std::mutex mu;  // guards scratch growth and the batch graph cache
 };
 
@@ -258,15 +287,16 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
         return fail(SEG_ERR_INVALID_ARG, "seg_label: unknown mode %d", (int)mode);
     if (n == 0) return SEG_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
     if (mode == SEG_MODE_PLAIN) {
+        ProfScope ps(&a->prof, PROF_PLAIN, st);
         cudaError_t e = launch_label_plain(atlas->view, d_fibers, n, d_labels, d_dist, d_cidx,
                                            d_orient, st, atlas->config[0]);
         return e ? cuda_fail(e, "seg_label: plain kernel") : SEG_OK;
     }
-    seg_atlas* a = const_cast<seg_atlas*>(atlas);
     return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n,
                       mode == SEG_MODE_GEMM_TF32, d_labels, d_dist, d_cidx, d_orient, st,
-                      a->config[(int)mode]);
+                      a->config[(int)mode], &a->prof);
 }
 
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,
@@ -287,6 +317,7 @@ seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* c
             return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: NULL buffer for subject %d", s);
     }
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    ProfScope ps(&a->prof, PROF_BATCH, (cudaStream_t)stream);
     return batch_launch(a->view, &a->gemm, &a->batch, &a->scratch, &a->mu, nsubj, h_fibers,
                         reinterpret_cast<const long long*>(h_counts), (int)mode, h_labels,
                         h_dist, (cudaStream_t)stream, a->config[(int)mode]);
@@ -314,6 +345,7 @@ seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
     if (n > 0 && (!d_fibers || !d_cidx || !d_orient))
         return fail(SEG_ERR_INVALID_ARG, "seg_grad: NULL fibers, cidx or orient");
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    ProfScope ps(&a->prof, PROF_GRAD, (cudaStream_t)stream);
     return grad_launch(a->view, a->inv_perm, &a->scratch, &a->mu, d_fibers, n, h_affine12,
                        d_cidx, d_orient, d_grad_affine12, d_grad_centroids, d_cost,
                        (cudaStream_t)stream);
@@ -362,6 +394,44 @@ seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64
     return grad_noalloc_launch(atlas->view, atlas->inv_perm, d_fibers, n, h_affine12, d_cidx,
                                d_orient, d_grad_affine12, d_grad_centroids, d_cost,
                                (cudaStream_t)stream);
+}
+
+seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_profile_enable: atlas is NULL");
+    std::lock_guard<std::mutex> lock(atlas->mu);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e) return cuda_fail(e, "seg_profile_enable");
+    atlas->prof.clear();
+    atlas->prof.enabled = enable != 0;
+    return SEG_OK;
+}
+
+seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launches,
+                            double* total_ms) {
+    g_last_error.clear();
+    if (!atlas || !kernel) return fail(SEG_ERR_INVALID_ARG, "seg_profile_read: NULL argument");
+    static const char* names[PROF_SLOTS] = {"plain", "batch", "gemm_prep", "gemm_screen",
+                                            "gemm_exact", "gemm_rescan", "gemm_finalize", "grad"};
+    int slot = -1;
+    for (int k = 0; k < PROF_SLOTS; ++k)
+        if (strcmp(kernel, names[k]) == 0) slot = k;
+    if (slot < 0) return fail(SEG_ERR_INVALID_ARG, "seg_profile_read: unknown kernel '%s'", kernel);
+    long long cnt = 0;
+    double ms = 0.0;
+    Profiler& p = atlas->prof;
+    for (size_t i = 0; i < p.used; ++i) {
+        if (p.slot_of[i] != slot) continue;
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(p.pool[i].second);
+        if (!e) e = cudaEventElapsedTime(&t, p.pool[i].first, p.pool[i].second);
+        if (e) return cuda_fail(e, "seg_profile_read");
+        ++cnt;
+        ms += t;
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = ms;
+    return SEG_OK;
 }
 
 seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {

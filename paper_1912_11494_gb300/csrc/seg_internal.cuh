@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cmath>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "seg_common.cuh"
 
@@ -12,6 +14,31 @@ namespace seg {
 
 seg_status fail(seg_status s, const char* fmt, ...);
 seg_status cuda_fail(cudaError_t e, const char* what);
+
+// Event-pair timing of the library's kernels (seg_profile_enable / seg_profile_read).
+enum ProfSlot { PROF_PLAIN = 0, PROF_BATCH, PROF_GEMM_PREP, PROF_GEMM_SCREEN, PROF_GEMM_EXACT,
+                PROF_GEMM_RESCAN, PROF_GEMM_FINAL, PROF_GRAD, PROF_SLOTS };
+struct Profiler {
+    bool enabled = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;  // reusable events
+    size_t used = 0;
+    std::vector<int> slot_of;                                // slot of each used pair
+    void begin(int slot, cudaStream_t st, cudaEvent_t* end_out);
+    void clear();
+    ~Profiler();
+};
+// RAII helper: records the start event now and the end event when it goes out of scope.
+struct ProfScope {
+    Profiler* p;
+    cudaStream_t st;
+    cudaEvent_t end = nullptr;
+    ProfScope(Profiler* prof, int slot, cudaStream_t s) : p(prof), st(s) {
+        if (p && p->enabled) p->begin(slot, st, &end);
+    }
+    ~ProfScope() {
+        if (end) cudaEventRecord(end, st);
+    }
+};
 
 // A growable device buffer owned by an atlas. Users lock the atlas mutex on the host and order
 // themselves on the device through `last_use`, so calls from different streams never overlap
@@ -38,7 +65,8 @@ void free_gemm_atlas(GemmAtlas* g);
 int gemm_num_configs();
 seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,
                       const float* fib, long long n, bool tf32, int* labels, float* dist,
-                      int* cidx, unsigned char* orient, cudaStream_t st, int config);
+                      int* cidx, unsigned char* orient, cudaStream_t st, int config,
+                      Profiler* prof = nullptr);
 
 // Cached CUDA graph of the batched launch: counter reset, work-table upload (from a pinned
 // host copy the host rewrites before each replay) and the persistent kernel.

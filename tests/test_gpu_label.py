@@ -188,3 +188,27 @@ def test_every_pair_passes_overflowing_queues(dev, mode):
         lab, dist, cidx, orient = run(at, fib, dev, mode)
         parity.compare(fib, a.centroids, a.bundle_of, thr, lab, dist, cidx, orient)
         assert np.all(lab >= 0)
+
+
+def test_profile_and_tune(dev, small_workload, tmp_path):
+    from paper_1912_11494_gb300 import tune
+    atlas_np, fib = small_workload
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    f = torch.as_tensor(fib, device=dev)
+    binding.seg_profile_enable(at, True)
+    run(at, fib, dev, "plain")
+    run(at, fib, dev, "gemm_bf16")
+    assert binding.seg_profile_read(at, "plain")[0] == 1
+    for k in ("gemm_prep", "gemm_screen", "gemm_exact", "gemm_finalize"):
+        c, ms = binding.seg_profile_read(at, k)
+        assert c == 1 and ms > 0
+    binding.seg_profile_enable(at, False)
+    assert binding.seg_profile_read(at, "plain") == (0, 0.0)
+    with pytest.raises(binding.SegError):
+        binding.seg_profile_read(at, "nope")
+    path = str(tmp_path / "tune.json")
+    r1 = tune.tune(at, f, "plain", path=path)
+    assert not r1["cached"] and 0 <= r1["config"] < binding.seg_num_configs("plain")
+    r2 = tune.tune(at, f, "plain", path=path)
+    assert r2["cached"] and r2["config"] == r1["config"]
+    assert binding.seg_get_config(at, "plain") == r1["config"]
