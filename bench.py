@@ -39,7 +39,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="best", choices=["best", "plain", "gemm_bf16", "gemm_tf32"])
+    p.add_argument("--mode", default="best", choices=["best", "plain", "gemm_bf16", "gemm_tf32",
+                                                      "gemm_inv_bf16", "gemm_inv_tf32"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--config", type=int, default=None, help="tile-shape config (default: tuned)")
     p.add_argument("--n", type=int, default=None, help="override the fiber count")
@@ -204,8 +205,9 @@ def _has_cuda():
 
 
 # ----------------------------------------------------------------------------- our arm
-MODES = ("plain", "gemm_bf16", "gemm_tf32")
-DOMINANT = {"plain": "plain", "gemm_bf16": "gemm_screen", "gemm_tf32": "gemm_screen"}
+MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32")
+DOMINANT = {"plain": "plain", "gemm_bf16": "gemm_screen", "gemm_tf32": "gemm_screen",
+            "gemm_inv_bf16": "gemm_screen", "gemm_inv_tf32": "gemm_screen"}
 KERNEL_NAME = {"plain": "k_label_plain", "gemm_screen": "k_gemm_screen"}
 LAUNCH_SLOTS = ("plain", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
                 "gemm_finalize")
@@ -378,21 +380,22 @@ def main():
                                           f"pairs"}
         else:
             bf16 = float(pk.get("bf16_tflops", 1900.0))
-            peak = bf16 if mode == "gemm_bf16" else bf16 * (1.1 / 2.25)
-            alg = 2.0 * n * 64 * 2 * atlas_np.M
+            peak = bf16 if mode.endswith("bf16") else bf16 * (1.1 / 2.25)
+            cols = atlas_np.M if "inv" in mode else 2 * atlas_np.M
+            alg = 2.0 * n * 64 * cols
             roofs[mode] = {"bound": "tensor", "kernel": KERNEL_NAME[kname],
                            "achieved": alg / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
-                           "peak_source": ("measured bf16 burst" if mode == "gemm_bf16" else
+                           "peak_source": ("measured bf16 burst" if mode.endswith("bf16") else
                                            "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)")
                                           + f" ({pk_src})",
-                           "algorithmic": f"2 x {n} fibers x K=64 x {2 * atlas_np.M} columns"}
+                           "algorithmic": f"2 x {n} fibers x K=64 x {cols} columns"}
         roofs[mode]["frac"] = roofs[mode]["achieved"] / roofs[mode]["peak"]
         roofs[mode]["traffic"] = traffic_for(KERNEL_NAME[kname])
         roofs[mode]["ms_per_launch"] = k["ms_per_launch"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if head == "plain" else ("bf16" if head == "gemm_bf16" else "tf32"),
+            "dtype": "f32" if head == "plain" else ("bf16" if head.endswith("bf16") else "tf32"),
             "data": "synthetic",
             "config": {"workload": args.workload, "fibers": n, "centroids": atlas_np.M,
                        "bundles": atlas_np.B, "points": 21, "mode": head,

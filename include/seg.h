@@ -59,7 +59,14 @@ typedef enum {
      * the reversed centroid, from a BF16 (or TF32) GEMM with FP32 accumulation and a rounding
      * margin. Labels and distances equal SEG_MODE_PLAIN's. Not in the paper. */
     SEG_MODE_GEMM_BF16 = 1,
-    SEG_MODE_GEMM_TF32 = 2
+    SEG_MODE_GEMM_TF32 = 2,
+    /* Tensor-core prune with an orientation-free bound, then the exact test (both
+     * orientations) on survivors. With c = a_10 and s_i = (a_i + a_(20-i))/2 (i < 10),
+     * I(a,b) = |c_a - c_b|^2 + 2 sum_i |s_i(a) - s_i(b)|^2 <= min over orientations of the
+     * 21-point sum <= 21 d_ME^2, one column per centroid (33 features + bias). Labels and
+     * distances equal SEG_MODE_PLAIN's. Not in the paper. */
+    SEG_MODE_GEMM_INV_BF16 = 3,
+    SEG_MODE_GEMM_INV_TF32 = 4
 } seg_mode;
 
 typedef struct seg_atlas seg_atlas; /* opaque; owns its device copies of the atlas */

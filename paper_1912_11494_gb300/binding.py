@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libseg.so")
 SEG_OK = 0
 STATUS_NAMES = {0: "SEG_OK", 1: "SEG_ERR_INVALID_ARG", 2: "SEG_ERR_CUDA", 3: "SEG_ERR_OOM",
                 4: "SEG_ERR_UNSUPPORTED", 5: "SEG_ERR_TIMEOUT", 6: "SEG_ERR_OVERFLOW"}
-MODES = {"plain": 0, "gemm_bf16": 1, "gemm_tf32": 2}
+MODES = {"plain": 0, "gemm_bf16": 1, "gemm_tf32": 2, "gemm_inv_bf16": 3, "gemm_inv_tf32": 4}
 NPTS = 21
 
 # Every entry point the header declares: (name, restype, argtypes).

@@ -60,8 +60,7 @@ seg_status batch_launch(const AtlasView& at, GemmAtlas* g, BatchState* b, Scratc
     if (mode != SEG_MODE_PLAIN) {
         for (int s = 0; s < nsubj; ++s) {
             if (counts[s] == 0) continue;
-            seg_status r = label_gemm(at, g, scratch, mu, fib[s], counts[s],
-                                      mode == SEG_MODE_GEMM_TF32, labels[s],
+            seg_status r = label_gemm(at, g, scratch, mu, fib[s], counts[s], mode, labels[s],
                                       dist ? dist[s] : nullptr, nullptr, nullptr, st, config);
             if (r != SEG_OK) return r;
         }

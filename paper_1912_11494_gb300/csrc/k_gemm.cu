@@ -27,6 +27,14 @@
 // merges the result into the fiber's packed key with atomicMin (same key as the plain kernel,
 // so the tie rule of Algorithm 1 holds); fibers whose survivors did not fit the list are
 // rescanned by an exact kernel; a last kernel writes labels and distances.
+//
+// Orientation-free variant (SEG_MODE_GEMM_INV_*). With c = a_10 and s_i = (a_i + a_(20-i))/2,
+// for x_i = a_i - b_i, y_i = a_(20-i) - b_(20-i) (or the reversed pairing) the identity
+// |x|^2 + |y|^2 = |x + y|^2 / 2 + |x - y|^2 / 2 >= |x + y|^2 / 2 gives, in either orientation,
+//     S >= |c_a - c_b|^2 + 2 sum_(i<10) |s_i(a) - s_i(b)|^2 = I(a, b),
+// and x + y is the same vector for both orientations, so I is one column per centroid over 33
+// features (c and sqrt(2) s_i) and the same separable margin applies. Survivors are checked in
+// both orientations.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -86,6 +94,58 @@ __device__ inline float tf32_up(float x) {  // round toward +inf at 10 mantissa 
     return __uint_as_float(u);
 }
 
+// Orientation-free features of 63 centred coordinates: c = point 10, then sqrt(2) s_i for
+// i = 0..9 with s_i the midpoint of points i and 20 - i (33 values).
+__device__ inline void inv_features(const float* x, float* f) {
+    f[0] = x[3 * CENTRE];
+    f[1] = x[3 * CENTRE + 1];
+    f[2] = x[3 * CENTRE + 2];
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            f[3 + 3 * i + r] = (x[3 * i + r] + x[3 * (NPTS - 1 - i) + r]) * 0.70710678118654752f;
+}
+
+constexpr int NF_INV = 33;  // orientation-free features
+
+// Orientation-free centroid columns: sorted centroid s at column s.
+__global__ void k_prep_b_inv(AtlasView at, int fmt, int cols, int cols_pad, void* out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols_pad) return;
+    float q[NF_INV];
+    float pad = PAD_NEG;
+    if (j < cols) {
+        const float* b = at.cen + (size_t)j * CROW;
+        float x[NC];
+        for (int i = 0; i < NPTS; ++i) {
+            x[3 * i] = b[3 * i] - at.c0x;
+            x[3 * i + 1] = b[3 * i + 1] - at.c0y;
+            x[3 * i + 2] = b[3 * i + 2] - at.c0z;
+        }
+        inv_features(x, q);
+        double n2 = 0.0;
+        for (int k = 0; k < NF_INV; ++k) n2 += (double)q[k] * q[k];
+        const double t2 = (double)at.thr2[j];
+        const double kap = kappa_of(fmt);
+        const double G = 0.5 * (n2 - 21.0 * t2 * (1.0 + RHO)) - 0.5 * kap * n2 -
+                         (1e-5 * (n2 + 21.0 * t2) + 0.005);
+        pad = (float)(-G);
+        if ((double)pad < -G) pad = nextafterf(pad, INFINITY);
+    } else {
+        for (int k = 0; k < NF_INV; ++k) q[k] = 0.0f;
+    }
+    if (fmt == 1) {
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)j * 64;
+        for (int k = 0; k < 63; ++k) o[k] = __float2bfloat16_rn(k < NF_INV ? q[k] : 0.0f);
+        o[63] = j < cols ? __float2bfloat16_ru(pad) : __float2bfloat16_rn(PAD_NEG);
+    } else {
+        float* o = reinterpret_cast<float*>(out) + (size_t)j * 64;
+        for (int k = 0; k < 63; ++k) o[k] = tf32_rn(k < NF_INV ? q[k] : 0.0f);
+        o[63] = j < cols ? tf32_up(pad) : tf32_rn(PAD_NEG);
+    }
+}
+
 // Centroid columns: sorted centroid s gives column 2s (points in order) and 2s+1 (reversed).
 __global__ void k_prep_b(AtlasView at, int fmt, int cols, int cols_pad, void* out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -132,7 +192,8 @@ constexpr int PREP_WARPS = 2;
 
 __global__ void __launch_bounds__(PREP_WARPS * 32)
 k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView at, int fmt,
-         void* __restrict__ out, float* __restrict__ alpha, unsigned long long* __restrict__ key) {
+         int inv, void* __restrict__ out, float* __restrict__ alpha,
+         unsigned long long* __restrict__ key) {
     __shared__ float s_in[PREP_WARPS][32 * NC];
     __shared__ uint32_t s_out[PREP_WARPS][32 * 65];  // 32 rows of up to 64 words, padded
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -160,6 +221,13 @@ k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView 
     if (!finite) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) p[k] = 0.0f;
+    } else if (inv) {
+        float fe[NF_INV];
+        inv_features(p, fe);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) p[k] = k < NF_INV ? fe[k] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < NF_INV; ++k) n2 += (double)p[k] * p[k];
     } else {
 #pragma unroll
         for (int k = 0; k < NC; ++k) n2 += (double)p[k] * p[k];
@@ -512,31 +580,81 @@ __device__ inline bool exact_one(const float* a, const float* b, float bound2, f
     return true;
 }
 
-// One thread per survivor record: the fiber is loaded once, then each surviving column of the
-// record (centroid s = column / 2, orientation = column % 2) runs the exact test.
-__global__ void k_exact_survivors(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
+// Exact test of the survivors. A warp takes 32 records, stages their 32 fiber rows in shared
+// memory with coalesced loads, and spreads the records' surviving columns evenly over its lanes
+// (prefix sum of the mask popcounts, __fns to find each lane's bit); each lane reads its
+// centroid row with sixteen 16-byte loads and runs the exact test: in the column's orientation
+// (directional bound) or in both (orientation-free bound).
+constexpr int EX_WARPS = 4;
+constexpr int EX_STRIDE = 65;  // padded fiber row in shared memory (conflict-free columns)
+
+template <bool INV>
+__global__ void __launch_bounds__(EX_WARPS * 32)
+k_exact_survivors(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
+    __shared__ float s_fib[EX_WARPS][32 * EX_STRIDE];
+    __shared__ uint4 s_rec[EX_WARPS][32];
+    __shared__ unsigned s_pre[EX_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long cnt = min((long long)*g.cnt, g.cap);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < cnt;
-         e += (long long)gridDim.x * blockDim.x) {
-        const uint4 rec = g.list[e];
-        const long long f = rec.x;
-        float a[NC];
-        const float* src = fib + f * NC;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) a[k] = __ldg(src + k);
-        unsigned mask = rec.z;
-        while (mask) {
-            const int bit = __ffs((int)mask) - 1;
-            mask &= mask - 1u;
-            const unsigned col = rec.y + (unsigned)bit;
-            const int s = (int)(col >> 1), o = (int)(col & 1u);
-            const float* b = at.cen + (size_t)s * CROW;  // read point by point (L1-resident)
-            const float bound =
-                fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
-            float d2;
-            const bool pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
-            if (pass) atomicMin(g.key + f, pack_key(d2, s, o));
+    float* sf = s_fib[w];
+    for (long long base = ((long long)blockIdx.x * EX_WARPS + w) * 32; base < cnt;
+         base += (long long)gridDim.x * EX_WARPS * 32) {
+        const bool have = base + lane < cnt;
+        const uint4 rec = have ? g.list[base + lane] : make_uint4(0u, 0u, 0u, 0u);
+        s_rec[w][lane] = rec;
+        const int nrec = (int)min(32LL, cnt - base);
+        for (int r = 0; r < nrec; ++r) {
+            const unsigned f = __shfl_sync(0xffffffffu, rec.x, r);
+            const float* src = fib + (size_t)f * NC;
+            sf[r * EX_STRIDE + lane] = __ldg(src + lane);
+            if (lane < NC - 32) sf[r * EX_STRIDE + 32 + lane] = __ldg(src + 32 + lane);
         }
+        unsigned incl = __popc(rec.z);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        s_pre[w][lane] = incl;
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (unsigned p0 = 0; p0 < total; p0 += 32) {
+            const unsigned p = p0 + (unsigned)lane;
+            if (p < total) {
+                int lo = 0, hi = 31;  // first record whose inclusive prefix exceeds p
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_pre[w][mid] > p) hi = mid; else lo = mid + 1;
+                }
+                const unsigned prev = lo ? s_pre[w][lo - 1] : 0u;
+                const uint4 rr = s_rec[w][lo];
+                const int bit = (int)__fns(rr.z, 0u, (int)(p - prev) + 1);
+                const unsigned col = rr.y + (unsigned)bit;
+                const int s = INV ? (int)col : (int)(col >> 1);
+                float b[CROW];
+                const float4* b4 = reinterpret_cast<const float4*>(at.cen + (size_t)s * CROW);
+#pragma unroll
+                for (int k = 0; k < CROW / 4; ++k) {
+                    const float4 t = __ldg(b4 + k);
+                    b[4 * k] = t.x;
+                    b[4 * k + 1] = t.y;
+                    b[4 * k + 2] = t.z;
+                    b[4 * k + 3] = t.w;
+                }
+                const float* a = sf + lo * EX_STRIDE;
+                const float bound =
+                    fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[rr.x] >> 32)));
+                float d2;
+                int o = INV ? 0 : (int)(col & 1u);
+                bool pass;
+                if (INV)
+                    pass = exact_pair(a, b, bound, d2, o);
+                else
+                    pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
+                if (pass) atomicMin(g.key + rr.x, pack_key(d2, s, o));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -672,27 +790,43 @@ seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st) {
     k_prep_b<<<blocks, threads, 0, st>>>(at, 1, g->cols, g->cols_pad, g->b_bf16);
     k_prep_b<<<blocks, threads, 0, st>>>(at, 2, g->cols, g->cols_pad, g->b_tf32);
     if ((e = cudaGetLastError())) return cuda_fail(e, "gemm operand prep");
+    g->cols_inv = at.M;
+    g->cols_inv_pad = (at.M + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
+    if ((e = cudaMalloc(&g->bi_bf16, (size_t)g->cols_inv_pad * 64 * 2)) ||
+        (e = cudaMalloc(&g->bi_tf32, (size_t)g->cols_inv_pad * 64 * 4)))
+        return cuda_fail(e, "gemm operands");
+    const int bi = (g->cols_inv_pad + threads - 1) / threads;
+    k_prep_b_inv<<<bi, threads, 0, st>>>(at, 1, g->cols_inv, g->cols_inv_pad, g->bi_bf16);
+    k_prep_b_inv<<<bi, threads, 0, st>>>(at, 2, g->cols_inv, g->cols_inv_pad, g->bi_tf32);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "gemm operand prep");
     return SEG_OK;
 }
 
 void free_gemm_atlas(GemmAtlas* g) {
     cudaFree(g->b_bf16);
     cudaFree(g->b_tf32);
+    cudaFree(g->bi_bf16);
+    cudaFree(g->bi_tf32);
     cudaFree(g->stats);
     *g = GemmAtlas{};
 }
 
 seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, std::mutex* mu,
-                      const float* fib, long long n, bool tf32, int* labels, float* dist,
+                      const float* fib, long long n, int mode, int* labels, float* dist,
                       int* cidx, unsigned char* orient, cudaStream_t st, int config,
                       Profiler* prof) {
+    const bool tf32 = mode == SEG_MODE_GEMM_TF32 || mode == SEG_MODE_GEMM_INV_TF32;
+    const bool inv = mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
     const int fmt = tf32 ? 2 : 1;
+    const int cols = inv ? ga->cols_inv : ga->cols;
+    const int cols_pad = inv ? ga->cols_inv_pad : ga->cols_pad;
+    const void* bop = inv ? (tf32 ? ga->bi_tf32 : ga->bi_bf16) : (tf32 ? ga->b_tf32 : ga->b_bf16);
     if (config < 0 || config >= kNumShapes) config = 0;
     const GemmShape sh = tf32 ? kTf32Shapes[config] : kBf16Shapes[config];
     const long long rows_per_unit = 128LL * sh.R;
     const long long n_units = (n + rows_per_unit - 1) / rows_per_unit;
     const long long n_pad = n_units * rows_per_unit;
-    const int n_tiles = ga->cols_pad / sh.N;
+    const int n_tiles = cols_pad / sh.N;
     if (n_pad >= (1LL << 32))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
     // survivor records (one per fiber per 32-column chunk with survivors): about 1.6 per fiber
@@ -726,8 +860,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
 
     cudaError_t e = cudaSuccess;
     CUtensorMap ta, tb;
-    if (!make_tmap(&ta, g.a, n_pad, fmt, 128) ||
-        !make_tmap(&tb, tf32 ? ga->b_tf32 : ga->b_bf16, ga->cols_pad, fmt, sh.N)) {
+    if (!make_tmap(&ta, g.a, n_pad, fmt, 128) || !make_tmap(&tb, bop, cols_pad, fmt, sh.N)) {
         scratch_release(scratch, st);
         return fail(SEG_ERR_CUDA, "seg_label: cuTensorMapEncodeTiled failed");
     }
@@ -737,16 +870,19 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
         k_prep_a<<<(unsigned)((n_pad + rows_per_block - 1) / rows_per_block), PREP_WARPS * 32, 0,
-                   st>>>(fib, n, n_pad, at, fmt, g.a, g.alpha, g.key);
+                   st>>>(fib, n, n_pad, at, fmt, inv ? 1 : 0, g.a, g.alpha, g.key);
         e = cudaGetLastError();
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_SCREEN, st);
-        e = dispatch_screen(sh, ta, tb, n_units, n_tiles, ga->cols, g, at.status, sms, st);
+        e = dispatch_screen(sh, ta, tb, n_units, n_tiles, cols, g, at.status, sms, st);
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
-        k_exact_survivors<<<sms * 8, 256, 0, st>>>(fib, at, g);
+        if (inv)
+            k_exact_survivors<true><<<sms * 8, EX_WARPS * 32, 0, st>>>(fib, at, g);
+        else
+            k_exact_survivors<false><<<sms * 8, EX_WARPS * 32, 0, st>>>(fib, at, g);
         e = cudaGetLastError();
     }
     if (!e) {
@@ -757,7 +893,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_FINAL, st);
         k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-            n, at, g, labels, dist, cidx, orient, n * (long long)ga->cols, ga->stats);
+            n, at, g, labels, dist, cidx, orient, n * (long long)cols, ga->stats);
         e = cudaGetLastError();
     }
     seg_status r = scratch_release(scratch, st);

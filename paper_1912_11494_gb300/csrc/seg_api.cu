@@ -124,7 +124,7 @@ struct seg_atlas {
     GemmAtlas gemm{};
     ScratchArena scratch{};
     BatchState batch{};
-    int config[3] = {0, 0, 0};  // tile-shape selection per seg_mode
+    int config[5] = {0, 0, 0, 0, 0};  // tile-shape selection per seg_mode
     Profiler prof;
     std::mutex mu;  // guards scratch growth and the batch graph cache
 };
@@ -283,7 +283,7 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld < 0", (long long)n);
     if (n > 0 && (!d_fibers || !d_labels))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: NULL fibers or labels");
-    if (mode != SEG_MODE_PLAIN && mode != SEG_MODE_GEMM_BF16 && mode != SEG_MODE_GEMM_TF32)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_GEMM_INV_TF32)
         return fail(SEG_ERR_INVALID_ARG, "seg_label: unknown mode %d", (int)mode);
     if (n == 0) return SEG_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -294,9 +294,8 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
                                            d_orient, st, atlas->config[0]);
         return e ? cuda_fail(e, "seg_label: plain kernel") : SEG_OK;
     }
-    return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n,
-                      mode == SEG_MODE_GEMM_TF32, d_labels, d_dist, d_cidx, d_orient, st,
-                      a->config[(int)mode], &a->prof);
+    return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n, (int)mode, d_labels,
+                      d_dist, d_cidx, d_orient, st, a->config[(int)mode], &a->prof);
 }
 
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,
@@ -308,7 +307,7 @@ seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* c
     if (nsubj == 0) return SEG_OK;
     if (!h_fibers || !h_counts || !h_labels)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: NULL pointer array");
-    if (mode != SEG_MODE_PLAIN && mode != SEG_MODE_GEMM_BF16 && mode != SEG_MODE_GEMM_TF32)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_GEMM_INV_TF32)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: unknown mode %d", (int)mode);
     for (int s = 0; s < nsubj; ++s) {
         if (h_counts[s] < 0)
@@ -355,7 +354,9 @@ int32_t seg_num_configs(seg_mode mode) {
     switch (mode) {
         case SEG_MODE_PLAIN: return kNumPlainConfigs;
         case SEG_MODE_GEMM_BF16:
-        case SEG_MODE_GEMM_TF32: return gemm_num_configs();
+        case SEG_MODE_GEMM_TF32:
+        case SEG_MODE_GEMM_INV_BF16:
+        case SEG_MODE_GEMM_INV_TF32: return gemm_num_configs();
     }
     return 0;
 }

@@ -58,13 +58,17 @@ struct GemmAtlas {
     int cols_pad = 0;         // cols rounded up to the N tile
     void* b_bf16 = nullptr;   // [cols_pad][64] bf16, centred, K-major
     void* b_tf32 = nullptr;   // [cols_pad][64] fp32 holding TF32-rounded values
+    int cols_inv = 0;         // M columns of orientation-free features (sorted centroid s at s)
+    int cols_inv_pad = 0;
+    void* bi_bf16 = nullptr;  // [cols_inv_pad][64]
+    void* bi_tf32 = nullptr;
     long long* stats = nullptr;  // [3] pairs, survivors, overflow fibers of the last call
 };
 seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st);
 void free_gemm_atlas(GemmAtlas* g);
 int gemm_num_configs();
 seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,
-                      const float* fib, long long n, bool tf32, int* labels, float* dist,
+                      const float* fib, long long n, int mode, int* labels, float* dist,
                       int* cidx, unsigned char* orient, cudaStream_t st, int config,
                       Profiler* prof = nullptr);
 

@@ -107,3 +107,52 @@ def test_margin_constants():
     # BF16's margin is four times TF32's; both exceed the plain 2u bound of two roundings
     assert kappa("bf16") > 2 * U["bf16"] and kappa("tf32") > 2 * U["tf32"]
     assert kappa("bf16") / kappa("tf32") == pytest.approx(4, rel=0.02)
+
+
+def inv_features(x):
+    """33 orientation-free features per fiber: centre point, sqrt(2) x midpoints of (i, 20-i)."""
+    x = np.asarray(x, np.float32)
+    c = x[:, 10]
+    m = ((x[:, :10] + x[:, 20:10:-1]) * np.float32(0.70710678118654752)).astype(np.float32)
+    return np.concatenate([c, m.reshape(len(x), 30)], axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+def test_orientation_free_prune_never_drops_an_accepted_centroid(small_workload, fmt):
+    """I(a,b) = |dc|^2 + 2 sum |ds_i|^2 <= 21 d_ME^2 (both orientations), plus the same margin:
+    every centroid the exact test accepts in either orientation survives."""
+    atlas, fib = small_workload
+    order = np.argsort(atlas.bundle_of, kind="stable")
+    cs = atlas.centroids[order]
+    th = atlas.thresholds[atlas.bundle_of[order]].astype(np.float32)
+    t2 = (th * th).astype(np.float32).astype(np.float64)
+    c0 = np.round(cs[:, 10].astype(np.float64).mean(0)).astype(np.float32)
+    P = inv_features((fib - c0).astype(np.float32))
+    Q = inv_features((cs - c0).astype(np.float32))
+    k = kappa(fmt)
+    pn = (P.astype(np.float64) ** 2).sum(1)
+    qn = (Q.astype(np.float64) ** 2).sum(1)
+    alpha = f32_round(0.5 * (1 - k) * pn - (1e-5 * pn + 0.005), "down").astype(np.float64)
+    G = 0.5 * (qn - 21 * t2 * (1 + RHO)) - 0.5 * k * qn - (1e-5 * (qn + 21 * t2) + 0.005)
+    rn, up = (bf16_rn, bf16_ru) if fmt == "bf16" else (tf32_rn, tf32_up)
+    Pt, Qt, pad = rn(P).astype(np.float64), rn(Q).astype(np.float64), up(f32_round(-G, "up"))
+    dot = Pt @ Qt.T + pad.astype(np.float64)[None, :]
+    mag = np.abs(Pt) @ np.abs(Qt).T + np.abs(pad.astype(np.float64))[None, :]
+    keep_worst = dot - GAMMA * mag >= alpha[:, None]
+    dme, _, _ = oracle.dme_matrix(fib, cs)
+    accepted = dme ** 2 <= t2[None, :] * (1 + 1e-6)
+    assert accepted.sum() > 1000
+    assert not (accepted & ~keep_worst).any()
+    assert (dot + GAMMA * mag >= alpha[:, None]).mean() < 0.05
+
+
+def test_orientation_free_identity_is_a_lower_bound():
+    """The identity behind the features on random fibers: I <= min(S_direct, S_reversed)."""
+    rng = np.random.default_rng(2)
+    A = rng.normal(0, 20, size=(30, 21, 3)).astype(np.float32)
+    B = rng.normal(0, 20, size=(40, 21, 3)).astype(np.float32)
+    FA, FB = inv_features(A).astype(np.float64), inv_features(B).astype(np.float64)
+    I = ((FA[:, None] - FB[None]) ** 2).sum(-1)
+    Sd = ((A[:, None].astype(np.float64) - B[None]) ** 2).sum((-1, -2))
+    Sr = ((A[:, None].astype(np.float64) - B[None, :, ::-1]) ** 2).sum((-1, -2))
+    assert np.all(I <= np.minimum(Sd, Sr) * (1 + 1e-6) + 1e-6)
