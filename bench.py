@@ -209,7 +209,7 @@ MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32")
 DOMINANT = {"plain": "plain", "gemm_bf16": "gemm_screen", "gemm_tf32": "gemm_screen",
             "gemm_inv_bf16": "gemm_screen", "gemm_inv_tf32": "gemm_screen"}
 KERNEL_NAME = {"plain": "k_label_plain", "gemm_screen": "k_gemm_screen"}
-LAUNCH_SLOTS = ("plain", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
+LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
                 "gemm_finalize")
 
 

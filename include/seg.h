@@ -190,7 +190,7 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
  * seg_profile_read waits for those events and returns, for one kernel name, the number of
  * launches and their summed duration in milliseconds since profiling was (re)enabled.
  * Kernel names: "plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
- * "gemm_finalize", "grad". Enabling (or disabling) clears what was recorded.
+ * "gemm_finalize", "grad", "gemm_sort". Enabling (or disabling) clears what was recorded.
  */
 seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable);
 seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launches,

@@ -237,7 +237,7 @@ def seg_gemm_stats(atlas: Atlas):
 
 
 PROFILED_KERNELS = ("plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
-                    "gemm_finalize", "grad")
+                    "gemm_finalize", "grad", "gemm_sort")
 
 
 def seg_profile_enable(atlas: Atlas, enable: bool = True):

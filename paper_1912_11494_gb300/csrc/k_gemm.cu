@@ -17,16 +17,19 @@
 // is rounded upward, and the slacks cover FP32 norms, the centring and the exact test's own
 // rounding (rho). Every pair the exact FP32 test would accept therefore survives the prune.
 //
-// Kernel. A persistent CTA per SM, warp-specialised: warp 0 issues TMA loads (R fiber tiles of
-// 128 rows per work unit, double-buffered, and a ring of S centroid tiles of N columns), warp 1
-// issues tcgen05.mma (M=128, N, K=64) into one of two TMEM accumulators of R*N columns, and warps
-// 2..5 read the other accumulator with tcgen05.ld.red, which returns each row's max over 32
-// columns: only when that max reaches alpha does the warp look at the individual values and
-// append the surviving (fiber, column) pairs to a global list (staged per warp in shared memory).
-// A second kernel runs the exact test of Section 2.3 on every survivor in its orientation and
-// merges the result into the fiber's packed key with atomicMin (same key as the plain kernel,
-// so the tie rule of Algorithm 1 holds); fibers whose survivors did not fit the list are
-// rescanned by an exact kernel; a last kernel writes labels and distances.
+// Kernels. A counting sort orders the fibers by the 4 mm cell of their centre point, so that
+// the 32 fibers of a warp have nearly the same survivors. The fiber operand is written in that
+// order. The screen is a persistent CTA per SM, warp-specialised: warp 0 issues TMA loads (R
+// fiber tiles of 128 rows per work unit, double-buffered, and a ring of S centroid tiles of N
+// columns), warp 1 issues tcgen05.mma (M=128, N, K=64) into one of two TMEM accumulators of R*N
+// columns, and eight epilogue warps read the other accumulator with tcgen05.ld.red, which
+// returns each row's max over 32 columns: only when that max reaches alpha in some row does the
+// warp compare the individual values and write a block record (32 fibers x 32 columns, one
+// column mask per fiber). A second kernel runs the exact test of Section 2.3 on every survivor
+// of every block and merges the result into the fiber's packed key with atomicMin (same key as
+// the plain kernel, so the tie rule of Algorithm 1 holds); fibers whose survivors did not fit
+// the record list are rescanned by an exact kernel; a last kernel writes labels and distances
+// in the caller's order.
 //
 // Orientation-free variant (SEG_MODE_GEMM_INV_*). With c = a_10 and s_i = (a_i + a_(20-i))/2,
 // for x_i = a_i - b_i, y_i = a_(20-i) - b_(20-i) (or the reversed pairing) the identity
@@ -50,7 +53,8 @@ namespace {
 constexpr int EPI_WARPS = 8;       // two epilogue warps per TMEM lane quarter
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA, then epilogue
 constexpr int COL_ALIGN = 256;     // columns padded to a multiple of this
-constexpr int STAGE_CAP = 128;     // survivor records staged per epilogue warp
+constexpr int SLOT_GRAB = 16;      // block records an epilogue warp reserves at a time
+constexpr unsigned EMPTY_SLOT = 0xFFFFFFFFu;  // header of a reserved record left unused
 constexpr unsigned long long NAN_KEY = ~0ull - 1ull;
 constexpr float PAD_NEG = -1e30f;  // pad of padding columns: never survives
 
@@ -66,15 +70,20 @@ __host__ __device__ inline double kappa_of(int fmt) {
     return 1.05 * (2.0 * u + u * u) + 2.0 * GAMMA_ACC;
 }
 
-// A survivor record: fiber, first column of a 32-column chunk, and the mask of its columns
-// that survived (one record per fiber per chunk with survivors).
+// Survivors are kept as block records: one per (32 sorted fibers) x (32-column chunk) block of
+// the product with at least one surviving element, holding the first fiber and column and one
+// 32-bit column mask per fiber. With fibers in locality order a block holds about two hundred
+// survivors on atlases shaped like the paper's, so the exact kernel stages its fiber and
+// centroid rows once for all of them.
 struct GemmScratch {
-    void* a;                      // fiber operand [n_pad][64]
-    float* alpha;                 // [n_pad]
+    void* a;                      // fiber operand [n_pad][64], rows in sorted order
+    const unsigned* perm;         // [n] sorted position -> the caller's fiber index
+    float* alpha;                 // [n_pad] (sorted order, as key and flag)
     unsigned long long* key;      // [n]
     unsigned char* flag;          // [n] survivors dropped for lack of list space
-    uint4* list;                  // [cap] records {fiber, col0, mask, 0}
-    unsigned long long* cnt;      // [0] records appended, [1] fibers flagged, [2] survivors
+    uint2* hdr;                   // [cap] {first sorted fiber, first column} or EMPTY_SLOT
+    unsigned* mask;               // [cap][32] surviving columns of each of the 32 fibers
+    unsigned long long* cnt;      // [0] records reserved, [1] fibers flagged, [2] survivors
     long long cap;
 };
 
@@ -185,39 +194,147 @@ __global__ void k_prep_b(AtlasView at, int fmt, int cols, int cols_pad, void* ou
     }
 }
 
-// Fiber rows: centred coordinates, 1 in the pad column, alpha_i; keys initialised. One warp
-// per 32 rows: the 32 x 63 input floats are read with coalesced loads into shared memory, each
-// lane converts one row, and the 32 output rows go back out with coalesced stores.
-constexpr int PREP_WARPS = 2;
+// ---- locality order --------------------------------------------------------------------------
+// Subjects arrive in arbitrary order, so the 32 fibers a warp of the screen reads would have
+// unrelated survivor columns. A counting sort on the cell of the centre point (4 mm cells, a 64^3
+// grid around the atlas centre, cells in Morton order) groups fibers that lie close together;
+// every later kernel addresses fibers by their sorted position and reads the caller's row
+// through perm[]. Results do not depend on the order (each fiber's key is its own minimum).
+constexpr int GRID_BITS = 6;                       // cells per axis = 64
+constexpr int NBINS = 1 << (3 * GRID_BITS);        // 262,144 cells
+constexpr int SCAN_BLOCK = 1024;                   // bins scanned per block
+constexpr int NTOP = NBINS / SCAN_BLOCK;           // 256 block totals
+constexpr float CELL_MM = 4.0f;
 
-__global__ void __launch_bounds__(PREP_WARPS * 32)
-k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView at, int fmt,
-         int inv, void* __restrict__ out, float* __restrict__ alpha,
-         unsigned long long* __restrict__ key) {
-    __shared__ float s_in[PREP_WARPS][32 * NC];
-    __shared__ uint32_t s_out[PREP_WARPS][32 * 65];  // 32 rows of up to 64 words, padded
+__device__ inline unsigned spread3(unsigned v) {   // 6 bits -> every third bit
+    unsigned r = 0;
+#pragma unroll
+    for (int b = 0; b < GRID_BITS; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+__device__ inline unsigned cell_of(float v, float c0) {
+    const float t = floorf((v - c0) * (1.0f / CELL_MM)) + (float)(1 << (GRID_BITS - 1));
+    return t >= 0.0f ? (unsigned)fminf(t, (float)((1 << GRID_BITS) - 1)) : 0u;  // NaN -> 0
+}
+
+__global__ void k_bin_count(const float* __restrict__ fib, long long n, AtlasView at,
+                            unsigned* __restrict__ bin, unsigned* __restrict__ hist) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* c = fib + i * NC + 3 * CENTRE;
+    const unsigned b = spread3(cell_of(__ldg(c), at.c0x)) |
+                       (spread3(cell_of(__ldg(c + 1), at.c0y)) << 1) |
+                       (spread3(cell_of(__ldg(c + 2), at.c0z)) << 2);
+    bin[i] = b;
+    atomicAdd(hist + b, 1u);
+}
+
+// Exclusive scan of each block of SCAN_BLOCK bins in place; block totals to top[].
+__global__ void __launch_bounds__(SCAN_BLOCK) k_bin_scan(unsigned* __restrict__ hist,
+                                                         unsigned* __restrict__ top) {
+    __shared__ unsigned s_w[SCAN_BLOCK / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const unsigned v = hist[blockIdx.x * SCAN_BLOCK + t];
+    unsigned x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned s = s_w[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        s_w[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    hist[blockIdx.x * SCAN_BLOCK + t] = x - v + (w ? s_w[w - 1] : 0u);
+    if (t == SCAN_BLOCK - 1) top[blockIdx.x] = x + (w ? s_w[w - 1] : 0u);
+}
+
+// Exclusive scan of the NTOP block totals (one warp, NTOP / 32 values per lane).
+__global__ void k_bin_scan_top(unsigned* __restrict__ top) {
+    constexpr int PER = NTOP / 32;
+    const int lane = threadIdx.x;
+    unsigned v[PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        v[k] = top[lane * PER + k];
+        s += v[k];
+    }
+    unsigned x = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    unsigned run = x - s;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        top[lane * PER + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void k_bin_scatter(const unsigned* __restrict__ bin, long long n,
+                              unsigned* __restrict__ hist, const unsigned* __restrict__ top,
+                              unsigned* __restrict__ perm) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned b = bin[i];
+    perm[__ldg(top + b / SCAN_BLOCK) + atomicAdd(hist + b, 1u)] = (unsigned)i;
+}
+
+// Fiber rows in sorted order: centred coordinates (or the orientation-free features), 1 in
+// the pad column, alpha_i; keys initialised. One warp per 32 rows: the rows perm[r0 .. r0+31]
+// are gathered with two coalesced loads each into shared memory, each lane converts one row,
+// and the 32 output rows go back out with coalesced stores.
+//
+// |p|^2 is summed in FP32 (fmaf, fixed order): the computed value is within 63 u_32 |p|^2 of the
+// exact one, so n2 (1 - 4e-6) rounded down is a lower bound, and alpha is evaluated with
+// downward rounding from it: alpha never exceeds (1 - kappa)/2 |p|^2 - 1e-5 |p|^2 - 0.005.
+constexpr int PREP_WARPS = 4;
+constexpr int PREP_STRIDE = 65;
+
+__global__ void __launch_bounds__(PREP_WARPS * 32, 4)
+k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long long n,
+         long long n_pad, AtlasView at, int fmt, int inv, void* __restrict__ out,
+         float* __restrict__ alpha, unsigned long long* __restrict__ key) {
+    __shared__ uint32_t s_buf[PREP_WARPS][32 * PREP_STRIDE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long r0 = ((long long)blockIdx.x * PREP_WARPS + w) * 32;
     if (r0 >= n_pad) return;
-    const long long rows_in = max(0LL, min(32LL, n - r0));
-    float* si = s_in[w];
-    const float* src = fib + r0 * NC;
-    for (int k = lane; k < rows_in * NC; k += 32) si[k] = __ldg(src + k);
+    const int rows_in = (int)max(0LL, min(32LL, n - r0));
+    float* si = reinterpret_cast<float*>(s_buf[w]);
+    const unsigned src_row = lane < rows_in ? __ldg(perm + r0 + lane) : 0u;
+#pragma unroll 4
+    for (int r = 0; r < rows_in; ++r) {
+        const float* src = fib + (size_t)__shfl_sync(0xffffffffu, src_row, r) * NC;
+        si[r * PREP_STRIDE + lane] = __ldg(src + lane);
+        if (lane < NC - 32) si[r * PREP_STRIDE + 32 + lane] = __ldg(src + 32 + lane);
+    }
     __syncwarp();
     const long long i = r0 + lane;
     float p[NC];
     bool finite = lane < rows_in;
-    double n2 = 0.0;
     if (finite) {
 #pragma unroll
         for (int t = 0; t < NPTS; ++t) {
-            p[3 * t] = si[lane * NC + 3 * t] - at.c0x;
-            p[3 * t + 1] = si[lane * NC + 3 * t + 1] - at.c0y;
-            p[3 * t + 2] = si[lane * NC + 3 * t + 2] - at.c0z;
+            p[3 * t] = si[lane * PREP_STRIDE + 3 * t] - at.c0x;
+            p[3 * t + 1] = si[lane * PREP_STRIDE + 3 * t + 1] - at.c0y;
+            p[3 * t + 2] = si[lane * PREP_STRIDE + 3 * t + 2] - at.c0z;
         }
 #pragma unroll
         for (int k = 0; k < NC; ++k) finite = finite && isfinite(p[k]);
     }
+    if (i < n) key[i] = finite ? ~0ull : NAN_KEY;  // a non-finite fiber gets the NaN key
+    float n2 = 0.0f;
     if (!finite) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) p[k] = 0.0f;
@@ -227,21 +344,18 @@ k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView 
 #pragma unroll
         for (int k = 0; k < NC; ++k) p[k] = k < NF_INV ? fe[k] : 0.0f;
 #pragma unroll
-        for (int k = 0; k < NF_INV; ++k) n2 += (double)p[k] * p[k];
+        for (int k = 0; k < NF_INV; ++k) n2 = fmaf(p[k], p[k], n2);
     } else {
 #pragma unroll
-        for (int k = 0; k < NC; ++k) n2 += (double)p[k] * p[k];
+        for (int k = 0; k < NC; ++k) n2 = fmaf(p[k], p[k], n2);
     }
-    const double kap = kappa_of(fmt);
-    const double al = 0.5 * (1.0 - kap) * n2 - (1e-5 * n2 + 0.005);
-    alpha[i] = finite ? __double2float_rd(al) : INFINITY;
-    if (i < n) {
-        bool fin_in = true;  // non-finite input (not only padding) gets the NaN key
-        for (int k = 0; k < NC; ++k) fin_in = fin_in && isfinite(si[lane * NC + k]);
-        key[i] = fin_in ? ~0ull : NAN_KEY;
-    }
-    uint32_t* so = s_out[w];
+    const float c1 = __double2float_rd(0.5 * (1.0 - kappa_of(fmt)) - 1e-5);
+    const float n2lo = __fmul_rd(n2, 0.999996f);
+    alpha[i] = finite ? __fmaf_rd(n2lo, c1, -0.005f) : INFINITY;
+    __syncwarp();  // every lane has its input row in registers: reuse the buffer for output
+    uint32_t* so = s_buf[w];
     const int words = fmt == 1 ? 32 : 64;  // 32-bit words per output row
+    const int stride = fmt == 1 ? 33 : 65;
     if (fmt == 1) {
 #pragma unroll
         for (int k = 0; k < 31; ++k) {
@@ -257,7 +371,6 @@ k_prep_a(const float* __restrict__ fib, long long n, long long n_pad, AtlasView 
     }
     __syncwarp();
     uint32_t* dst = reinterpret_cast<uint32_t*>(out) + r0 * words;
-    const int stride = fmt == 1 ? 33 : 65;
     for (int k = lane; k < 32 * words; k += 32) dst[k] = so[(k / words) * stride + (k % words)];
 }
 
@@ -275,8 +388,7 @@ struct GemmCfg {
     static constexpr int ACC_COLS = R * N;                    // TMEM columns per accumulator
     static constexpr int A_OFF = 0;
     static constexpr int B_OFF = A_OFF + ABUF * R * A_TILE;
-    static constexpr int ST_OFF = B_OFF + S * B_TILE;         // survivor staging
-    static constexpr int BAR_OFF = ST_OFF + EPI_WARPS * STAGE_CAP * 16;
+    static constexpr int BAR_OFF = B_OFF + S * B_TILE;
     static constexpr int NBAR = 2 * ABUF + 2 * S + 5;
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16 + 1024;  // + alignment slack
     static_assert(2 * ACC_COLS <= 512, "two accumulators must fit TMEM");
@@ -311,28 +423,25 @@ struct Waiter {
     }
 };
 
-__device__ inline void flush_stage(uint4* st, int& scnt, const GemmScratch& g, int lane) {
-    if (scnt == 0) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(g.cnt, (unsigned long long)scnt);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    unsigned surv = 0;
-    for (int i = lane; i < scnt; i += 32) {
-        const uint4 e = st[i];
-        surv += __popc(e.z);
-        if ((long long)(base + i) < g.cap) {
-            g.list[base + i] = e;
-        } else if (g.flag[e.x] == 0) {
-            g.flag[e.x] = 1;
-            atomicAdd(g.cnt + 1, 1ull);
+// One epilogue warp's reservation of block records (SLOT_GRAB at a time from the global count).
+struct SlotGrab {
+    unsigned long long next = 0, end = 0;
+    __device__ unsigned long long take(const GemmScratch& g, int lane) {
+        if (next == end) {
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(g.cnt, (unsigned long long)SLOT_GRAB);
+            next = __shfl_sync(0xffffffffu, b, 0);
+            end = next + SLOT_GRAB;
         }
+        return next++;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
-    if (lane == 0) atomicAdd(g.cnt + 2, (unsigned long long)surv);
-    __syncwarp();
-    scnt = 0;
-}
+    // mark the reserved records this warp did not use, so the exact kernel skips them
+    __device__ void close(const GemmScratch& g, int lane) {
+        for (unsigned long long b = next + lane; b < end; b += 32)
+            if ((long long)b < g.cap) g.hdr[b] = make_uint2(EMPTY_SLOT, 0u);
+        next = end;
+    }
+};
 
 template <int FMT, int R, int N, int S, int ABUF>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
@@ -485,11 +594,10 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         constexpr int CHUNKS = R * CPR;           // chunks per accumulator
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
-        uint4* st = reinterpret_cast<uint4*>(smem + C::ST_OFF) + (warp - 2) * STAGE_CAP;
-        int scnt = 0;
+        SlotGrab slots;
+        unsigned long long surv = 0;
         long long tile = 0;
         bool ok = true;
-        const unsigned lt = (1u << lane) - 1u;
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
             float al[4];
 #pragma unroll
@@ -518,22 +626,25 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         const int r = c / CPR;
                         const float a = r == 0 ? al[0] : r == 1 ? al[1] : r == 2 ? al[2] : al[3];
                         if (!__any_sync(0xffffffffu, mx[h] >= a)) continue;
-                        // rare: this lane's surviving columns of the chunk as a bit mask,
-                        // appended as one record (warp-aggregated)
+                        // rare: each lane's surviving columns of the chunk as a bit mask; the
+                        // warp's 32 masks form one block record
                         const unsigned col0 = (unsigned)(t * N + (c % CPR) * 32);
                         unsigned mask = 0;
 #pragma unroll
                         for (int i = 0; i < 32; ++i) mask |= (v[h][i] >= a ? 1u : 0u) << i;
                         if (col0 + 32 > (unsigned)cols)
                             mask &= col0 >= (unsigned)cols ? 0u : (1u << (cols - col0)) - 1u;
-                        if (scnt + 32 > STAGE_CAP) flush_stage(st, scnt, g, lane);
-                        const bool p = mask != 0u;
-                        const unsigned m = __ballot_sync(0xffffffffu, p);
-                        if (p)
-                            st[scnt + __popc(m & lt)] =
-                                make_uint4(fib0 + (unsigned)(r * 128), col0, mask, 0u);
-                        scnt += __popc(m);
-                        __syncwarp();
+                        if (!__any_sync(0xffffffffu, mask != 0u)) continue;
+                        surv += __popc(mask);
+                        const unsigned long long b = slots.take(g, lane);
+                        const unsigned f = fib0 + (unsigned)(r * 128);
+                        if ((long long)b < g.cap) {
+                            g.mask[b * 32 + lane] = mask;
+                            if (lane == 0) g.hdr[b] = make_uint2(f - (unsigned)lane, col0);
+                        } else if (mask != 0u && g.flag[f] == 0) {
+                            g.flag[f] = 1;  // no room: the fiber is rescanned exactly
+                            atomicAdd(g.cnt + 1, 1ull);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -542,7 +653,10 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
         }
         __syncwarp();
-        flush_stage(st, scnt, g, lane);
+        slots.close(g, lane);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+        if (lane == 0 && surv) atomicAdd(g.cnt + 2, surv);
     }
     // drain: make sure no TMA copy is still landing in this CTA's shared memory
     __syncthreads();
@@ -580,81 +694,104 @@ __device__ inline bool exact_one(const float* a, const float* b, float bound2, f
     return true;
 }
 
-// Exact test of the survivors. A warp takes 32 records, stages their 32 fiber rows in shared
-// memory with coalesced loads, and spreads the records' surviving columns evenly over its lanes
-// (prefix sum of the mask popcounts, __fns to find each lane's bit); each lane reads its
-// centroid row with sixteen 16-byte loads and runs the exact test: in the column's orientation
-// (directional bound) or in both (orientation-free bound).
-constexpr int EX_WARPS = 4;
-constexpr int EX_STRIDE = 65;  // padded fiber row in shared memory (conflict-free columns)
+// Exact test of the survivors, one block record per warp at a time. The warp copies (cp.async)
+// the rows of the block's fibers that have survivors and the rows of the union of its surviving
+// centroids into shared memory, then spreads the block's (fiber, column) pairs over its lanes
+// (prefix sum of the mask popcounts, __fns for each lane's bit) and runs the exact test from
+// shared memory: in the column's orientation (directional columns) or in both (orientation-free
+// columns), bounded by min(theta^2, the fiber's best so far).
+constexpr int EX_WARPS = 2;  // 33 KB of static shared memory per block
+constexpr int EX_STRIDE = 65;  // padded row in shared memory: lanes on different rows never
+                               // share a bank
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// bit k of the result = bit 2k or bit 2k+1 of x (centroid k of a directional 32-column chunk)
+__device__ __forceinline__ unsigned fold_pairs(unsigned x) {
+    x = (x | (x >> 1)) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0x0000FFFFu;
+}
 
 template <bool INV>
 __global__ void __launch_bounds__(EX_WARPS * 32)
-k_exact_survivors(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
+k_exact_blocks(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
     __shared__ float s_fib[EX_WARPS][32 * EX_STRIDE];
-    __shared__ uint4 s_rec[EX_WARPS][32];
+    __shared__ float s_cen[EX_WARPS][32 * EX_STRIDE];
     __shared__ unsigned s_pre[EX_WARPS][32];
+    __shared__ unsigned s_msk[EX_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long cnt = min((long long)*g.cnt, g.cap);
     float* sf = s_fib[w];
-    for (long long base = ((long long)blockIdx.x * EX_WARPS + w) * 32; base < cnt;
-         base += (long long)gridDim.x * EX_WARPS * 32) {
-        const bool have = base + lane < cnt;
-        const uint4 rec = have ? g.list[base + lane] : make_uint4(0u, 0u, 0u, 0u);
-        s_rec[w][lane] = rec;
-        const int nrec = (int)min(32LL, cnt - base);
-        for (int r = 0; r < nrec; ++r) {
-            const unsigned f = __shfl_sync(0xffffffffu, rec.x, r);
-            const float* src = fib + (size_t)f * NC;
-            sf[r * EX_STRIDE + lane] = __ldg(src + lane);
-            if (lane < NC - 32) sf[r * EX_STRIDE + 32 + lane] = __ldg(src + 32 + lane);
+    float* sc = s_cen[w];
+    for (long long blk = (long long)blockIdx.x * EX_WARPS + w; blk < cnt;
+         blk += (long long)gridDim.x * EX_WARPS) {
+        const uint2 h = g.hdr[blk];
+        if (h.x == EMPTY_SLOT) continue;
+        const unsigned m = g.mask[blk * 32 + lane];
+        // fiber rows with survivors
+        const unsigned orow = m ? __ldg(g.perm + h.x + lane) : 0u;
+        for (unsigned rows = __ballot_sync(0xffffffffu, m != 0u); rows; rows &= rows - 1) {
+            const int r = __ffs(rows) - 1;
+            const float* src = fib + (size_t)__shfl_sync(0xffffffffu, orow, r) * NC;
+            cp_async4(sf + r * EX_STRIDE + lane, src + lane);
+            if (lane < NC - 32) cp_async4(sf + r * EX_STRIDE + 32 + lane, src + 32 + lane);
         }
-        unsigned incl = __popc(rec.z);
+        // centroid rows of the union of the masks
+        const unsigned uni = __reduce_or_sync(0xffffffffu, m);
+        const unsigned s0 = INV ? h.y : h.y >> 1;
+        for (unsigned cr = INV ? uni : fold_pairs(uni); cr; cr &= cr - 1) {
+            const int j = __ffs(cr) - 1;
+            const float* src = at.cen + (size_t)(s0 + j) * CROW;
+            cp_async4(sc + j * EX_STRIDE + lane, src + lane);
+            if (lane < NC - 32) cp_async4(sc + j * EX_STRIDE + 32 + lane, src + 32 + lane);
+        }
+        unsigned incl = __popc(m);
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += v;
         }
         s_pre[w][lane] = incl;
+        s_msk[w][lane] = m;
         const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        cp_async_wait_all();
         __syncwarp();
         for (unsigned p0 = 0; p0 < total; p0 += 32) {
             const unsigned p = p0 + (unsigned)lane;
             if (p < total) {
-                int lo = 0, hi = 31;  // first record whose inclusive prefix exceeds p
+                int lo = 0, hi = 31;  // first fiber whose inclusive prefix exceeds p
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (s_pre[w][mid] > p) hi = mid; else lo = mid + 1;
                 }
                 const unsigned prev = lo ? s_pre[w][lo - 1] : 0u;
-                const uint4 rr = s_rec[w][lo];
-                const int bit = (int)__fns(rr.z, 0u, (int)(p - prev) + 1);
-                const unsigned col = rr.y + (unsigned)bit;
-                const int s = INV ? (int)col : (int)(col >> 1);
-                float b[CROW];
-                const float4* b4 = reinterpret_cast<const float4*>(at.cen + (size_t)s * CROW);
-#pragma unroll
-                for (int k = 0; k < CROW / 4; ++k) {
-                    const float4 t = __ldg(b4 + k);
-                    b[4 * k] = t.x;
-                    b[4 * k + 1] = t.y;
-                    b[4 * k + 2] = t.z;
-                    b[4 * k + 3] = t.w;
-                }
+                const int bit = (int)__fns(s_msk[w][lo], 0u, (int)(p - prev) + 1);
+                const int s = (int)s0 + (INV ? bit : bit >> 1);
                 const float* a = sf + lo * EX_STRIDE;
+                const float* b = sc + (INV ? bit : bit >> 1) * EX_STRIDE;
+                const unsigned f = h.x + (unsigned)lo;
                 const float bound =
-                    fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[rr.x] >> 32)));
+                    fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
                 float d2;
-                int o = INV ? 0 : (int)(col & 1u);
+                int o = INV ? 0 : (bit & 1);
                 bool pass;
                 if (INV)
                     pass = exact_pair(a, b, bound, d2, o);
                 else
                     pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
-                if (pass) atomicMin(g.key + rr.x, pack_key(d2, s, o));
+                if (pass) atomicMin(g.key + f, pack_key(d2, s, o));
             }
         }
-        __syncwarp();
+        __syncwarp();  // the buffers are refilled for the next record
     }
 }
 
@@ -663,9 +800,10 @@ __global__ void k_overflow_rescan(const float* __restrict__ fib, long long n, At
                                   GemmScratch g) {
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n || g.flag[f] == 0) return;
+    const float* src = fib + (size_t)g.perm[f] * NC;
     float a[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) a[k] = __ldg(fib + f * NC + k);
+    for (int k = 0; k < NC; ++k) a[k] = __ldg(src + k);
     for (int s = 0; s < at.M; ++s) {
         const float bound = fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
         float d2;
@@ -687,18 +825,19 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __rest
     }
     if (f >= n) return;
     const unsigned long long k = g.key[f];
+    const unsigned o = g.perm[f];  // results go to the caller's order
     if (k == NAN_KEY || k == ~0ull) {
-        labels[f] = -1;
-        if (dist) dist[f] = k == NAN_KEY ? NAN : INFINITY;
-        if (cidx) cidx[f] = -1;
-        if (orient) orient[f] = 0;
+        labels[o] = -1;
+        if (dist) dist[o] = k == NAN_KEY ? NAN : INFINITY;
+        if (cidx) cidx[o] = -1;
+        if (orient) orient[o] = 0;
         return;
     }
     const int s = (int)((k & 0xffffffffull) >> 1);
-    labels[f] = at.bundle[s];
-    if (dist) dist[f] = sqrtf(__uint_as_float((unsigned)(k >> 32)));
-    if (cidx) cidx[f] = at.perm[s];
-    if (orient) orient[f] = (unsigned char)(k & 1ull);
+    labels[o] = at.bundle[s];
+    if (dist) dist[o] = sqrtf(__uint_as_float((unsigned)(k >> 32)));
+    if (cidx) cidx[o] = at.perm[s];
+    if (orient) orient[o] = (unsigned char)(k & 1ull);
 }
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -829,16 +968,21 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const int n_tiles = cols_pad / sh.N;
     if (n_pad >= (1LL << 32))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
-    // survivor records (one per fiber per 32-column chunk with survivors): about 1.6 per fiber
-    // on atlases shaped like the paper's; room for 8 per fiber + slack
-    const long long cap = n * 8 + (1 << 20);
+    // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for 16
+    // per 32 fibers + slack (fibers past the room are rescanned exactly)
+    const long long cap = n_pad / 32 * 16 + 65536;
     const size_t elem = tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * 64 * elem);
     const size_t off_key = off_alpha + align256((size_t)n_pad * 4);
     const size_t off_flag = off_key + align256((size_t)n * 8);
     const size_t off_cnt = off_flag + align256((size_t)n);
-    const size_t off_list = off_cnt + 256;
-    const size_t bytes = off_list + (size_t)cap * 16;
+    const size_t off_perm = off_cnt + 256;
+    const size_t off_bin = off_perm + align256((size_t)n * 4);
+    const size_t off_hist = off_bin + align256((size_t)n * 4);
+    const size_t off_top = off_hist + (size_t)NBINS * 4;
+    const size_t off_hdr = off_top + (size_t)NTOP * 4;
+    const size_t off_mask = off_hdr + align256((size_t)cap * 8);
+    const size_t bytes = off_mask + (size_t)cap * 128;
 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -855,7 +999,13 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     g.key = reinterpret_cast<unsigned long long*>(b8 + off_key);
     g.flag = b8 + off_flag;
     g.cnt = reinterpret_cast<unsigned long long*>(b8 + off_cnt);
-    g.list = reinterpret_cast<uint4*>(b8 + off_list);
+    g.hdr = reinterpret_cast<uint2*>(b8 + off_hdr);
+    g.mask = reinterpret_cast<unsigned*>(b8 + off_mask);
+    unsigned* perm = reinterpret_cast<unsigned*>(b8 + off_perm);
+    unsigned* bin = reinterpret_cast<unsigned*>(b8 + off_bin);
+    unsigned* hist = reinterpret_cast<unsigned*>(b8 + off_hist);
+    unsigned* top = reinterpret_cast<unsigned*>(b8 + off_top);
+    g.perm = perm;
     g.cap = cap;
 
     cudaError_t e = cudaSuccess;
@@ -867,10 +1017,20 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) e = cudaMemsetAsync(g.cnt, 0, 256, st);
     if (!e) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
     if (!e) {
+        ProfScope ps(prof, PROF_GEMM_SORT, st);
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        e = cudaMemsetAsync(hist, 0, (size_t)NBINS * 4, st);
+        if (!e) k_bin_count<<<nb, 256, 0, st>>>(fib, n, at, bin, hist);
+        if (!e) k_bin_scan<<<NTOP, SCAN_BLOCK, 0, st>>>(hist, top);
+        if (!e) k_bin_scan_top<<<1, 32, 0, st>>>(top);
+        if (!e) k_bin_scatter<<<nb, 256, 0, st>>>(bin, n, hist, top, perm);
+        if (!e) e = cudaGetLastError();
+    }
+    if (!e) {
         ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
         k_prep_a<<<(unsigned)((n_pad + rows_per_block - 1) / rows_per_block), PREP_WARPS * 32, 0,
-                   st>>>(fib, n, n_pad, at, fmt, inv ? 1 : 0, g.a, g.alpha, g.key);
+                   st>>>(fib, perm, n, n_pad, at, fmt, inv ? 1 : 0, g.a, g.alpha, g.key);
         e = cudaGetLastError();
     }
     if (!e) {
@@ -880,9 +1040,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
         if (inv)
-            k_exact_survivors<true><<<sms * 8, EX_WARPS * 32, 0, st>>>(fib, at, g);
+            k_exact_blocks<true><<<sms * 6, EX_WARPS * 32, 0, st>>>(fib, at, g);
         else
-            k_exact_survivors<false><<<sms * 8, EX_WARPS * 32, 0, st>>>(fib, at, g);
+            k_exact_blocks<false><<<sms * 6, EX_WARPS * 32, 0, st>>>(fib, at, g);
         e = cudaGetLastError();
     }
     if (!e) {

@@ -413,7 +413,8 @@ seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launc
     g_last_error.clear();
     if (!atlas || !kernel) return fail(SEG_ERR_INVALID_ARG, "seg_profile_read: NULL argument");
     static const char* names[PROF_SLOTS] = {"plain", "batch", "gemm_prep", "gemm_screen",
-                                            "gemm_exact", "gemm_rescan", "gemm_finalize", "grad"};
+                                            "gemm_exact", "gemm_rescan", "gemm_finalize", "grad",
+                                            "gemm_sort"};
     int slot = -1;
     for (int k = 0; k < PROF_SLOTS; ++k)
         if (strcmp(kernel, names[k]) == 0) slot = k;

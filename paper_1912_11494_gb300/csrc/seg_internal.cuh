@@ -17,7 +17,7 @@ seg_status cuda_fail(cudaError_t e, const char* what);
 
 // Event-pair timing of the library's kernels (seg_profile_enable / seg_profile_read).
 enum ProfSlot { PROF_PLAIN = 0, PROF_BATCH, PROF_GEMM_PREP, PROF_GEMM_SCREEN, PROF_GEMM_EXACT,
-                PROF_GEMM_RESCAN, PROF_GEMM_FINAL, PROF_GRAD, PROF_SLOTS };
+                PROF_GEMM_RESCAN, PROF_GEMM_FINAL, PROF_GRAD, PROF_GEMM_SORT, PROF_SLOTS };
 struct Profiler {
     bool enabled = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;  // reusable events

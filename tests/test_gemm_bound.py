@@ -6,7 +6,9 @@ column and alpha a per-fiber constant (see k_gemm.cu). This test re-derives thos
 numpy with the same rounding rules, takes the worst case of the FP32 accumulation, and checks on
 every pair of the 10,000 x 1,000 workload that each pair the exact test accepts (FP64 d_ME of
 that orientation within the threshold) survives. It also reports the prune rate. The bound
-itself (max over points >= mean over points) is the plain inequality max >= mean.
+itself (max over points >= mean over points) is the plain inequality max >= mean. The kernel
+evaluates alpha from an FP32 norm with downward rounding, so its alpha never exceeds the FP64
+value used here and it keeps at least every pair this test keeps.
 """
 import numpy as np
 import pytest

@@ -159,6 +159,27 @@ def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
         assert st["overflow_fibers"] == 0
 
 
+@pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_bf16", "gemm_inv_tf32"])
+def test_gemm_locality_order_extremes(dev, mode):
+    """The GEMM modes visit fibers in the order of their centre point's 4 mm cell. Centres far
+    outside the cell grid (clamped to its border), thousands of fibers in one cell, and a NaN
+    centre (sorted to cell 0) still give the plain kernel's results in the caller's order."""
+    a = synth.make_atlas(30, per_bundle=20, seed=41)
+    base = synth.make_subject(a, 3000, 0.8, seed=42)
+    same = np.repeat(base[:1], 2500, axis=0) + np.random.default_rng(43).normal(
+        0, 0.3, size=(2500, 21, 3)).astype(np.float32)           # one hot cell
+    far = base[:700] + np.array([900.0, -1200.0, 3000.0], np.float32)  # outside the grid
+    fib = np.concatenate([base, same, far]).astype(np.float32)
+    fib[5, 10, 0] = np.nan                                        # NaN centre point
+    fib = fib[np.random.default_rng(44).permutation(len(fib))]
+    at = make_atlas(a.centroids, a.bundle_of, a.thresholds, dev)
+    ref = run(at, fib, dev, "plain")
+    got = run(at, fib, dev, mode)
+    for x, y in zip(ref, got):
+        np.testing.assert_array_equal(x, y)
+    parity.compare(fib, a.centroids, a.bundle_of, a.thresholds, *got)
+
+
 def test_every_tile_shape_identical(dev, small_workload):
     """All tile-shape configurations of a mode compute the same labels, distances, centroids."""
     atlas_np, fib = small_workload
@@ -200,7 +221,7 @@ def test_profile_and_tune(dev, small_workload, tmp_path):
     run(at, fib, dev, "plain")
     run(at, fib, dev, "gemm_bf16")
     assert binding.seg_profile_read(at, "plain")[0] == 1
-    for k in ("gemm_prep", "gemm_screen", "gemm_exact", "gemm_finalize"):
+    for k in ("gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_finalize"):
         c, ms = binding.seg_profile_read(at, k)
         assert c == 1 and ms > 0
     binding.seg_profile_enable(at, False)
