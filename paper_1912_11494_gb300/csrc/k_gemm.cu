@@ -78,6 +78,7 @@ __host__ __device__ inline double kappa_of(int fmt) {
 struct GemmScratch {
     void* a;                      // fiber operand [n_pad][64], rows in sorted order
     const unsigned* perm;         // [n] sorted position -> the caller's fiber index
+    float* fs;                    // [n_pad][64] the fibers in sorted order (63 floats + 0)
     float* alpha;                 // [n_pad] (sorted order, as key and flag)
     unsigned long long* key;      // [n]
     unsigned char* flag;          // [n] survivors dropped for lack of list space
@@ -305,7 +306,8 @@ constexpr int PREP_STRIDE = 65;
 __global__ void __launch_bounds__(PREP_WARPS * 32, 4)
 k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long long n,
          long long n_pad, AtlasView at, int fmt, int inv, void* __restrict__ out,
-         float* __restrict__ alpha, unsigned long long* __restrict__ key) {
+         float* __restrict__ alpha, unsigned long long* __restrict__ key,
+         float* __restrict__ fs) {
     __shared__ uint32_t s_buf[PREP_WARPS][32 * PREP_STRIDE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long r0 = ((long long)blockIdx.x * PREP_WARPS + w) * 32;
@@ -320,6 +322,13 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
         if (lane < NC - 32) si[r * PREP_STRIDE + 32 + lane] = __ldg(src + 32 + lane);
     }
     __syncwarp();
+    // the sorted copy of the rows (read by the exact re-check)
+    float* fdst = fs + r0 * CROW;
+#pragma unroll 4
+    for (int k = lane; k < 32 * CROW; k += 32) {
+        const int r = k / CROW, c = k % CROW;
+        fdst[k] = (c < NC && r < rows_in) ? si[r * PREP_STRIDE + c] : 0.0f;
+    }
     const long long i = r0 + lane;
     float p[NC];
     bool finite = lane < rows_in;
@@ -694,104 +703,191 @@ __device__ inline bool exact_one(const float* a, const float* b, float bound2, f
     return true;
 }
 
-// Exact test of the survivors, one block record per warp at a time. The warp copies (cp.async)
-// the rows of the block's fibers that have survivors and the rows of the union of its surviving
-// centroids into shared memory, then spreads the block's (fiber, column) pairs over its lanes
-// (prefix sum of the mask popcounts, __fns for each lane's bit) and runs the exact test from
-// shared memory: in the column's orientation (directional columns) or in both (orientation-free
-// columns), bounded by min(theta^2, the fiber's best so far).
-constexpr int EX_WARPS = 2;  // 33 KB of static shared memory per block
-constexpr int EX_STRIDE = 65;  // padded row in shared memory: lanes on different rows never
-                               // share a bank
+// Exact test of the survivors, one block record per CTA at a time. The CTA copies (cp.async) the
+// block's 32 fiber rows (contiguous in the sorted copy) and the chunk's centroid rows into shared
+// memory, with theta^2 beside each centroid and each fiber's best d^2 so far; the next record's
+// header and masks are loaded while the current one is tested. The block's (fiber, column) pairs are numbered by a prefix sum of
+// the mask popcounts. Phase A runs test1 and test2 (Section 2.3) on every pair and queues the
+// pairs with a live orientation; phase B runs test3 and test4 on the queue, so that the lanes of
+// a warp do the same stage of the test. The bound is min(theta^2, the fiber's best so far);
+// exits are strict (> bound), so equal distances still reach the atomicMin of the packed key and
+// the tie rule of Algorithm 1 holds.
+constexpr int EX_THREADS = 128;
+constexpr int EX_STRIDE = 65;    // padded centroid row in shared memory: lanes on different
+                                 // rows never share a bank
+constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
+constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// bit k of the result = bit 2k or bit 2k+1 of x (centroid k of a directional 32-column chunk)
-__device__ __forceinline__ unsigned fold_pairs(unsigned x) {
-    x = (x | (x >> 1)) & 0x55555555u;
-    x = (x | (x >> 1)) & 0x33333333u;
-    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
-    x = (x | (x >> 4)) & 0x00FF00FFu;
-    return (x | (x >> 8)) & 0x0000FFFFu;
+// Stages of the exact test in orientation O (0: points in order, 1: reversed as in Eq. 2).
+template <int O>
+__device__ __forceinline__ float ends2(const float* a, const float* b) {
+    constexpr int L = NPTS - 1;
+    return fmaxf(pd2(a, 0, b, O ? L : 0), pd2(a, L, b, O ? 0 : L));
+}
+template <int O>
+__device__ __forceinline__ float mid4(const float* a, const float* b, float m) {
+    constexpr int L = NPTS - 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) m = fmaxf(m, pd2(a, test3_point(q), b, O ? L - test3_point(q) : test3_point(q)));
+    return m;
+}
+template <int O>
+__device__ __forceinline__ float rest17(const float* a, const float* b, float m) {
+    constexpr int L = NPTS - 1;
+#pragma unroll
+    for (int i = 1; i < L; ++i)
+        if (!is_early_point(i)) m = fmaxf(m, pd2(a, i, b, O ? L - i : i));
+    return m;
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(EX_WARPS * 32)
-k_exact_blocks(const float* __restrict__ fib, AtlasView at, GemmScratch g) {
-    __shared__ float s_fib[EX_WARPS][32 * EX_STRIDE];
-    __shared__ float s_cen[EX_WARPS][32 * EX_STRIDE];
-    __shared__ unsigned s_pre[EX_WARPS][32];
-    __shared__ unsigned s_msk[EX_WARPS][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__global__ void __launch_bounds__(EX_THREADS)
+k_exact_blocks(AtlasView at, GemmScratch g) {
+    __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
+    __shared__ float s_cen[32 * EX_STRIDE];  // slot 64 of a row: theta^2 of its centroid
+    __shared__ unsigned s_pre[32], s_msk[32], s_best[32];
+    __shared__ unsigned s_q[EX_QCAP];        // fiber | bit << 5 | direct alive << 10 | rev << 11
+    __shared__ float2 s_qm[EX_QCAP];         // partial maxima of the queued pairs
+    __shared__ unsigned s_nq;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const long long cnt = min((long long)*g.cnt, g.cap);
-    float* sf = s_fib[w];
-    float* sc = s_cen[w];
-    for (long long blk = (long long)blockIdx.x * EX_WARPS + w; blk < cnt;
-         blk += (long long)gridDim.x * EX_WARPS) {
-        const uint2 h = g.hdr[blk];
+    long long blk = blockIdx.x;
+    uint2 hn = make_uint2(EMPTY_SLOT, 0u);  // the next record's header and masks, loaded one
+    unsigned mn = 0u;                       // record ahead
+    if (blk < cnt) {
+        hn = g.hdr[blk];
+        mn = g.mask[blk * 32 + lane];
+    }
+    for (; blk < cnt; blk += gridDim.x) {
+        const uint2 h = hn;
+        const unsigned m = mn;
+        if (blk + gridDim.x < cnt) {
+            hn = g.hdr[blk + gridDim.x];
+            mn = g.mask[(blk + gridDim.x) * 32 + lane];
+        }
         if (h.x == EMPTY_SLOT) continue;
-        const unsigned m = g.mask[blk * 32 + lane];
-        // fiber rows with survivors
-        const unsigned orow = m ? __ldg(g.perm + h.x + lane) : 0u;
-        for (unsigned rows = __ballot_sync(0xffffffffu, m != 0u); rows; rows &= rows - 1) {
-            const int r = __ffs(rows) - 1;
-            const float* src = fib + (size_t)__shfl_sync(0xffffffffu, orow, r) * NC;
-            cp_async4(sf + r * EX_STRIDE + lane, src + lane);
-            if (lane < NC - 32) cp_async4(sf + r * EX_STRIDE + 32 + lane, src + 32 + lane);
-        }
-        // centroid rows of the union of the masks
-        const unsigned uni = __reduce_or_sync(0xffffffffu, m);
         const unsigned s0 = INV ? h.y : h.y >> 1;
-        for (unsigned cr = INV ? uni : fold_pairs(uni); cr; cr &= cr - 1) {
-            const int j = __ffs(cr) - 1;
-            const float* src = at.cen + (size_t)(s0 + j) * CROW;
-            cp_async4(sc + j * EX_STRIDE + lane, src + lane);
-            if (lane < NC - 32) cp_async4(sc + j * EX_STRIDE + 32 + lane, src + 32 + lane);
-        }
-        unsigned incl = __popc(m);
+        // the 32 sorted fiber rows (16-byte copies) and the chunk's centroid rows (4-byte
+        // copies into conflict-free rows), theta^2 beside each centroid
+        const float* fsrc = g.fs + (size_t)h.x * CROW;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
+        for (int c = tid; c < 32 * (CROW / 4); c += EX_THREADS)
+            cp_async16(s_fib + (c >> 4) * FS_STRIDE + 4 * (c & 15), fsrc + 4 * c);
+        const int ncen = min(INV ? 32 : 16, at.M - (int)s0);
+        const float* csrc = at.cen + (size_t)s0 * CROW;
+        for (int c = tid; c < ncen * CROW; c += EX_THREADS)
+            cp_async4(s_cen + (c >> 6) * EX_STRIDE + (c & 63), csrc + c);
+        if (tid < ncen) s_cen[tid * EX_STRIDE + 64] = __ldg(at.thr2 + s0 + tid);
+        if (w == 0) {
+            unsigned incl = __popc(m);
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            s_pre[lane] = incl;
+            s_msk[lane] = m;
+            s_best[lane] = m ? (unsigned)(g.key[h.x + lane] >> 32) : 0xFFFFFFFFu;
+            if (lane == 0) s_nq = 0;
         }
-        s_pre[w][lane] = incl;
-        s_msk[w][lane] = m;
-        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
         cp_async_wait_all();
-        __syncwarp();
-        for (unsigned p0 = 0; p0 < total; p0 += 32) {
-            const unsigned p = p0 + (unsigned)lane;
+        __syncthreads();
+        const unsigned total = s_pre[31];
+        // phase A: test1 and test2 on every pair
+        for (unsigned p0 = 0; p0 < total; p0 += EX_THREADS) {
+            const unsigned p = p0 + (unsigned)tid;
+            bool push = false;
+            unsigned ent = 0;
+            float md = 0.0f, mr = 0.0f;
             if (p < total) {
                 int lo = 0, hi = 31;  // first fiber whose inclusive prefix exceeds p
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (s_pre[w][mid] > p) hi = mid; else lo = mid + 1;
+                    if (s_pre[mid] > p) hi = mid; else lo = mid + 1;
                 }
-                const unsigned prev = lo ? s_pre[w][lo - 1] : 0u;
-                const int bit = (int)__fns(s_msk[w][lo], 0u, (int)(p - prev) + 1);
-                const int s = (int)s0 + (INV ? bit : bit >> 1);
-                const float* a = sf + lo * EX_STRIDE;
-                const float* b = sc + (INV ? bit : bit >> 1) * EX_STRIDE;
-                const unsigned f = h.x + (unsigned)lo;
-                const float bound =
-                    fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
-                float d2;
-                int o = INV ? 0 : (bit & 1);
-                bool pass;
-                if (INV)
-                    pass = exact_pair(a, b, bound, d2, o);
-                else
-                    pass = o ? exact_one<1>(a, b, bound, d2) : exact_one<0>(a, b, bound, d2);
-                if (pass) atomicMin(g.key + f, pack_key(d2, s, o));
+                const unsigned prev = lo ? s_pre[lo - 1] : 0u;
+                const int bit = (int)__fns(s_msk[lo], 0u, (int)(p - prev) + 1);
+                const float* a = s_fib + lo * FS_STRIDE;
+                const float* b = s_cen + (INV ? bit : bit >> 1) * EX_STRIDE;
+                const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
+                const float c = pd2(a, CENTRE, b, CENTRE);
+                if (c <= bound) {
+                    bool ad, ar = false;
+                    if (INV) {
+                        md = fmaxf(c, ends2<0>(a, b));
+                        mr = fmaxf(c, ends2<1>(a, b));
+                        ad = md <= bound;
+                        ar = mr <= bound;
+                    } else {
+                        md = fmaxf(c, (bit & 1) ? ends2<1>(a, b) : ends2<0>(a, b));
+                        ad = md <= bound;
+                    }
+                    push = ad || ar;
+                    ent = (unsigned)lo | ((unsigned)bit << 5) | ((unsigned)ad << 10) |
+                          ((unsigned)ar << 11);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, push);
+            unsigned base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&s_nq, (unsigned)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (push) {
+                const unsigned q = base + __popc(bal & lt);
+                s_q[q] = ent;
+                s_qm[q] = make_float2(md, mr);
             }
         }
-        __syncwarp();  // the buffers are refilled for the next record
+        __syncthreads();
+        // phase B: test3 and test4 on the queued pairs
+        const unsigned nq = s_nq;
+        for (unsigned q = tid; q < nq; q += EX_THREADS) {
+            const unsigned ent = s_q[q];
+            const float2 mm = s_qm[q];
+            const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
+            const int j = INV ? bit : bit >> 1;
+            const float* a = s_fib + lo * FS_STRIDE;
+            const float* b = s_cen + j * EX_STRIDE;
+            // the best may have improved since phase A: a tighter bound discards only pairs
+            // that are strictly worse than a pair already merged
+            const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
+            float md = mm.x, mr = mm.y, d2;
+            int o;
+            bool pass;
+            if (INV) {
+                bool ad = ((ent >> 10) & 1u) && md <= bound;
+                bool ar = ((ent >> 11) & 1u) && mr <= bound;
+                if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; }
+                if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; }
+                if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; }
+                if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; }
+                pass = ad || ar;
+                if (ad && (!ar || md <= mr)) { d2 = md; o = 0; } else { d2 = mr; o = 1; }
+            } else {
+                o = bit & 1;
+                pass = md <= bound;
+                if (pass) { md = o ? mid4<1>(a, b, md) : mid4<0>(a, b, md); pass = md <= bound; }
+                if (pass) { md = o ? rest17<1>(a, b, md) : rest17<0>(a, b, md); pass = md <= bound; }
+                d2 = md;
+            }
+            if (pass) {
+                atomicMin(g.key + h.x + lo, pack_key(d2, (int)s0 + j, o));
+                atomicMin(s_best + lo, __float_as_uint(d2));
+            }
+        }
+        __syncthreads();  // the buffers are refilled for the next record
     }
 }
 
@@ -800,7 +896,7 @@ __global__ void k_overflow_rescan(const float* __restrict__ fib, long long n, At
                                   GemmScratch g) {
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n || g.flag[f] == 0) return;
-    const float* src = fib + (size_t)g.perm[f] * NC;
+    const float* src = g.fs + (size_t)f * CROW;
     float a[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) a[k] = __ldg(src + k);
@@ -980,7 +1076,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const size_t off_bin = off_perm + align256((size_t)n * 4);
     const size_t off_hist = off_bin + align256((size_t)n * 4);
     const size_t off_top = off_hist + (size_t)NBINS * 4;
-    const size_t off_hdr = off_top + (size_t)NTOP * 4;
+    const size_t off_fs = off_top + (size_t)NTOP * 4;
+    const size_t off_hdr = off_fs + (size_t)n_pad * CROW * 4;
     const size_t off_mask = off_hdr + align256((size_t)cap * 8);
     const size_t bytes = off_mask + (size_t)cap * 128;
 
@@ -1006,6 +1103,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     unsigned* hist = reinterpret_cast<unsigned*>(b8 + off_hist);
     unsigned* top = reinterpret_cast<unsigned*>(b8 + off_top);
     g.perm = perm;
+    g.fs = reinterpret_cast<float*>(b8 + off_fs);
     g.cap = cap;
 
     cudaError_t e = cudaSuccess;
@@ -1030,7 +1128,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
         k_prep_a<<<(unsigned)((n_pad + rows_per_block - 1) / rows_per_block), PREP_WARPS * 32, 0,
-                   st>>>(fib, perm, n, n_pad, at, fmt, inv ? 1 : 0, g.a, g.alpha, g.key);
+                   st>>>(fib, perm, n, n_pad, at, fmt, inv ? 1 : 0, g.a, g.alpha, g.key, g.fs);
         e = cudaGetLastError();
     }
     if (!e) {
@@ -1040,9 +1138,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
         if (inv)
-            k_exact_blocks<true><<<sms * 6, EX_WARPS * 32, 0, st>>>(fib, at, g);
+            k_exact_blocks<true><<<sms * 7, EX_THREADS, 0, st>>>(at, g);
         else
-            k_exact_blocks<false><<<sms * 6, EX_WARPS * 32, 0, st>>>(fib, at, g);
+            k_exact_blocks<false><<<sms * 7, EX_THREADS, 0, st>>>(at, g);
         e = cudaGetLastError();
     }
     if (!e) {
