@@ -204,12 +204,14 @@ seg_status seg_sync_status(const seg_atlas* atlas, void* stream);
 
 /*
  * Statistics of the last GEMM-mode seg_label on this atlas (read after the stream finished):
- * pairs = fibers x 2M (fiber, centroid, orientation) candidates screened, survivors = those
- * kept by the tensor-core bound, overflow_fibers = fibers rescanned by the exact kernel because
- * the survivor list was full. Any pointer may be NULL.
+ * pairs = fibers x columns (2M directional, or M orientation-free) candidates, screened = the
+ * candidates inside the (128-fiber x N-column) blocks the tensor cores computed (blocks whose
+ * centre-point boxes lie farther apart than every threshold are skipped; padding included),
+ * survivors = candidates kept by the tensor-core bound, overflow_fibers = fibers rescanned by
+ * the exact kernel because the survivor list was full. Any pointer may be NULL.
  */
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
-                          int64_t* overflow_fibers);
+                          int64_t* overflow_fibers, int64_t* screened);
 
 #ifdef __cplusplus
 }

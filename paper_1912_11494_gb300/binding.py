@@ -40,6 +40,7 @@ SIGNATURES = [
     ("seg_set_config", ctypes.c_int, [_P, ctypes.c_int, _I32]),
     ("seg_get_config", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I32)]),
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                      ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
     ("seg_profile_enable", ctypes.c_int, [_P, _I32]),
     ("seg_profile_read", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64),
@@ -231,9 +232,10 @@ def seg_sync_status(atlas: Atlas, stream=None):
 
 
 def seg_gemm_stats(atlas: Atlas):
-    p, s, o = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    _check(lib().seg_gemm_stats(atlas.handle, ctypes.byref(p), ctypes.byref(s), ctypes.byref(o)))
-    return dict(pairs=p.value, survivors=s.value, overflow_fibers=o.value)
+    p, s, o, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().seg_gemm_stats(atlas.handle, ctypes.byref(p), ctypes.byref(s), ctypes.byref(o),
+                                ctypes.byref(c)))
+    return dict(pairs=p.value, survivors=s.value, overflow_fibers=o.value, screened=c.value)
 
 
 PROFILED_KERNELS = ("plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",

@@ -21,7 +21,7 @@
 // the 32 fibers of a warp have nearly the same survivors. The fiber operand is written in that
 // order. The screen is a persistent CTA per SM, warp-specialised: warp 0 issues TMA loads (R
 // fiber tiles of 128 rows per work unit, double-buffered, and a ring of S centroid tiles of N
-// columns), warp 1 issues tcgen05.mma (M=128, N, K=64) into one of two TMEM accumulators of R*N
+// columns), warp 1 issues tcgen05.mma (M=128, N, K) into one of 512/(R*N) TMEM accumulators of R*N
 // columns, and eight epilogue warps read the other accumulator with tcgen05.ld.red, which
 // returns each row's max over 32 columns: only when that max reaches alpha in some row does the
 // warp compare the individual values and write a block record (32 fibers x 32 columns, one
@@ -36,8 +36,11 @@
 // |x|^2 + |y|^2 = |x + y|^2 / 2 + |x - y|^2 / 2 >= |x + y|^2 / 2 gives, in either orientation,
 //     S >= |c_a - c_b|^2 + 2 sum_(i<10) |s_i(a) - s_i(b)|^2 = I(a, b),
 // and x + y is the same vector for both orientations, so I is one column per centroid over 33
-// features (c and sqrt(2) s_i) and the same separable margin applies. Survivors are checked in
-// both orientations.
+// features (c and sqrt(2) s_i) and the same separable margin applies. The same inequality,
+// |u|^2 + |v|^2 >= |u + v|^2 / 2 with u = dc and v = sqrt(2) ds_9, merges the centre point and
+// the innermost midpoint into g = c / sqrt(2) + s_9, which leaves 30 features and the pad column
+// within K = 32: half the tensor-core work of the 64-wide directional operands. Survivors are
+// checked in both orientations.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -82,9 +85,15 @@ struct GemmScratch {
     float* alpha;                 // [n_pad] (sorted order, as key and flag)
     unsigned long long* key;      // [n]
     unsigned char* flag;          // [n] survivors dropped for lack of list space
+    const float4* ubox;           // [n_pad / 32][2] centre-point box of 32 sorted fibers
+    const float4* tbox;           // [n_tiles][2] centre-point box of a column tile, max theta^2
+    const float* cen_sp;          // the atlas's spatial-order arrays (GemmAtlas)
+    const float* thr2_sp;
+    const int* sp_s;
     uint2* hdr;                   // [cap] {first sorted fiber, first column} or EMPTY_SLOT
     unsigned* mask;               // [cap][32] surviving columns of each of the 32 fibers
-    unsigned long long* cnt;      // [0] records reserved, [1] fibers flagged, [2] survivors
+    unsigned long long* cnt;      // [0] records reserved, [1] fibers flagged, [2] survivors,
+                                  // [3] pairs in the blocks the tensor cores computed
     long long cap;
 };
 
@@ -104,29 +113,34 @@ __device__ inline float tf32_up(float x) {  // round toward +inf at 10 mantissa 
     return __uint_as_float(u);
 }
 
-// Orientation-free features of 63 centred coordinates: c = point 10, then sqrt(2) s_i for
-// i = 0..9 with s_i the midpoint of points i and 20 - i (33 values).
+// Orientation-free features of 63 centred coordinates (30 values): g = c / sqrt(2) + s_9, then
+// sqrt(2) s_i for i = 0..8, with c = point 10 and s_i the midpoint of points i and 20 - i.
 __device__ inline void inv_features(const float* x, float* f) {
-    f[0] = x[3 * CENTRE];
-    f[1] = x[3 * CENTRE + 1];
-    f[2] = x[3 * CENTRE + 2];
 #pragma unroll
-    for (int i = 0; i < 10; ++i)
+    for (int r = 0; r < 3; ++r)
+        f[r] = x[3 * CENTRE + r] * 0.70710678118654752f + (x[27 + r] + x[33 + r]) * 0.5f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             f[3 + 3 * i + r] = (x[3 * i + r] + x[3 * (NPTS - 1 - i) + r]) * 0.70710678118654752f;
 }
 
-constexpr int NF_INV = 33;  // orientation-free features
+constexpr int NF_INV = 30;  // orientation-free features
+constexpr int KE_INV = 32;  // their K width: 30 features, a zero, the pad column
+constexpr int KE_DIR = 64;  // K width of the directional columns: 63 coordinates, the pad
 
-// Orientation-free centroid columns: sorted centroid s at column s.
-__global__ void k_prep_b_inv(AtlasView at, int fmt, int cols, int cols_pad, void* out) {
+// Orientation-free centroid columns: the centroid at spatial position j in column j, rows of
+// KE_INV values.
+__global__ void k_prep_b_inv(AtlasView at, const int* sp_s, int fmt, int cols, int cols_pad,
+                             void* out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cols_pad) return;
     float q[NF_INV];
     float pad = PAD_NEG;
     if (j < cols) {
-        const float* b = at.cen + (size_t)j * CROW;
+        const int sj = sp_s[j];
+        const float* b = at.cen + (size_t)sj * CROW;
         float x[NC];
         for (int i = 0; i < NPTS; ++i) {
             x[3 * i] = b[3 * i] - at.c0x;
@@ -136,7 +150,7 @@ __global__ void k_prep_b_inv(AtlasView at, int fmt, int cols, int cols_pad, void
         inv_features(x, q);
         double n2 = 0.0;
         for (int k = 0; k < NF_INV; ++k) n2 += (double)q[k] * q[k];
-        const double t2 = (double)at.thr2[j];
+        const double t2 = (double)at.thr2[sj];
         const double kap = kappa_of(fmt);
         const double G = 0.5 * (n2 - 21.0 * t2 * (1.0 + RHO)) - 0.5 * kap * n2 -
                          (1e-5 * (n2 + 21.0 * t2) + 0.005);
@@ -146,24 +160,26 @@ __global__ void k_prep_b_inv(AtlasView at, int fmt, int cols, int cols_pad, void
         for (int k = 0; k < NF_INV; ++k) q[k] = 0.0f;
     }
     if (fmt == 1) {
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)j * 64;
-        for (int k = 0; k < 63; ++k) o[k] = __float2bfloat16_rn(k < NF_INV ? q[k] : 0.0f);
-        o[63] = j < cols ? __float2bfloat16_ru(pad) : __float2bfloat16_rn(PAD_NEG);
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)j * KE_INV;
+        for (int k = 0; k < KE_INV - 1; ++k) o[k] = __float2bfloat16_rn(k < NF_INV ? q[k] : 0.0f);
+        o[KE_INV - 1] = j < cols ? __float2bfloat16_ru(pad) : __float2bfloat16_rn(PAD_NEG);
     } else {
-        float* o = reinterpret_cast<float*>(out) + (size_t)j * 64;
-        for (int k = 0; k < 63; ++k) o[k] = tf32_rn(k < NF_INV ? q[k] : 0.0f);
-        o[63] = j < cols ? tf32_up(pad) : tf32_rn(PAD_NEG);
+        float* o = reinterpret_cast<float*>(out) + (size_t)j * KE_INV;
+        for (int k = 0; k < KE_INV - 1; ++k) o[k] = tf32_rn(k < NF_INV ? q[k] : 0.0f);
+        o[KE_INV - 1] = j < cols ? tf32_up(pad) : tf32_rn(PAD_NEG);
     }
 }
 
-// Centroid columns: sorted centroid s gives column 2s (points in order) and 2s+1 (reversed).
-__global__ void k_prep_b(AtlasView at, int fmt, int cols, int cols_pad, void* out) {
+// Directional centroid columns: the centroid at spatial position c gives column 2c (points in
+// order) and 2c+1 (reversed).
+__global__ void k_prep_b(AtlasView at, const int* sp_s, int fmt, int cols, int cols_pad,
+                         void* out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cols_pad) return;
     float q[NC];
     float pad = PAD_NEG;
     if (j < cols) {
-        const int s = j >> 1, o = j & 1;
+        const int s = sp_s[j >> 1], o = j & 1;
         const float* b = at.cen + (size_t)s * CROW;
         double n2 = 0.0;
         for (int i = 0; i < NPTS; ++i) {
@@ -303,11 +319,12 @@ __global__ void k_bin_scatter(const unsigned* __restrict__ bin, long long n,
 constexpr int PREP_WARPS = 4;
 constexpr int PREP_STRIDE = 65;
 
+template <int FMT, bool INV>
 __global__ void __launch_bounds__(PREP_WARPS * 32, 4)
 k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long long n,
-         long long n_pad, AtlasView at, int fmt, int inv, void* __restrict__ out,
+         long long n_pad, AtlasView at, void* __restrict__ out,
          float* __restrict__ alpha, unsigned long long* __restrict__ key,
-         float* __restrict__ fs) {
+         float* __restrict__ fs, float4* __restrict__ ubox) {
     __shared__ uint32_t s_buf[PREP_WARPS][32 * PREP_STRIDE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long r0 = ((long long)blockIdx.x * PREP_WARPS + w) * 32;
@@ -343,11 +360,29 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
         for (int k = 0; k < NC; ++k) finite = finite && isfinite(p[k]);
     }
     if (i < n) key[i] = finite ? ~0ull : NAN_KEY;  // a non-finite fiber gets the NaN key
+    {   // centre-point box of the warp's finite fibers (empty: lo = +inf, hi = -inf)
+        float lo[3], hi[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float c = finite ? si[lane * PREP_STRIDE + 3 * CENTRE + r] : 0.0f;
+            lo[r] = finite ? c : INFINITY;
+            hi[r] = finite ? c : -INFINITY;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                lo[r] = fminf(lo[r], __shfl_xor_sync(0xffffffffu, lo[r], off));
+                hi[r] = fmaxf(hi[r], __shfl_xor_sync(0xffffffffu, hi[r], off));
+            }
+        }
+        if (lane == 0) {
+            ubox[2 * (r0 / 32)] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+            ubox[2 * (r0 / 32) + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+        }
+    }
     float n2 = 0.0f;
     if (!finite) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) p[k] = 0.0f;
-    } else if (inv) {
+    } else if (INV) {
         float fe[NF_INV];
         inv_features(p, fe);
 #pragma unroll
@@ -358,25 +393,26 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
 #pragma unroll
         for (int k = 0; k < NC; ++k) n2 = fmaf(p[k], p[k], n2);
     }
-    const float c1 = __double2float_rd(0.5 * (1.0 - kappa_of(fmt)) - 1e-5);
+    const float c1 = __double2float_rd(0.5 * (1.0 - kappa_of(FMT)) - 1e-5);
     const float n2lo = __fmul_rd(n2, 0.999996f);
     alpha[i] = finite ? __fmaf_rd(n2lo, c1, -0.005f) : INFINITY;
     __syncwarp();  // every lane has its input row in registers: reuse the buffer for output
     uint32_t* so = s_buf[w];
-    const int words = fmt == 1 ? 32 : 64;  // 32-bit words per output row
-    const int stride = fmt == 1 ? 33 : 65;
-    if (fmt == 1) {
+    constexpr int KE = INV ? KE_INV : KE_DIR;     // row: KE - 1 values, then the pad column 1
+    constexpr int words = FMT == 1 ? KE / 2 : KE;  // 32-bit words per output row
+    constexpr int stride = words + 1;
+    if (FMT == 1) {
 #pragma unroll
-        for (int k = 0; k < 31; ++k) {
+        for (int k = 0; k < words - 1; ++k) {
             __nv_bfloat162 b = __floats2bfloat162_rn(p[2 * k], p[2 * k + 1]);
-            so[lane * 33 + k] = *reinterpret_cast<uint32_t*>(&b);
+            so[lane * stride + k] = *reinterpret_cast<uint32_t*>(&b);
         }
-        __nv_bfloat162 b = __floats2bfloat162_rn(p[62], 1.0f);
-        so[lane * 33 + 31] = *reinterpret_cast<uint32_t*>(&b);
+        __nv_bfloat162 b = __floats2bfloat162_rn(p[KE - 2], 1.0f);
+        so[lane * stride + words - 1] = *reinterpret_cast<uint32_t*>(&b);
     } else {
 #pragma unroll
-        for (int k = 0; k < 63; ++k) so[lane * 65 + k] = __float_as_uint(tf32_rn(p[k]));
-        so[lane * 65 + 63] = __float_as_uint(1.0f);
+        for (int k = 0; k < words - 1; ++k) so[lane * stride + k] = __float_as_uint(tf32_rn(p[k]));
+        so[lane * stride + words - 1] = __float_as_uint(1.0f);
     }
     __syncwarp();
     uint32_t* dst = reinterpret_cast<uint32_t*>(out) + r0 * words;
@@ -385,24 +421,94 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
 
 // ---- the tensor-core screen ------------------------------------------------------------------
 
-template <int FMT, int R, int N, int S, int ABUF>
+// ---- block culling ---------------------------------------------------------------------------
+// d_ME(a, b) >= |a_10 - b_10| in both orientations (the centre point pairs with itself, Eq. 2),
+// so a (work unit x column tile) block whose centre-point boxes are farther apart than the
+// largest threshold of the tile holds no pair that can pass: the screen skips it. The slack
+// covers the FP32 rounding of the box distance and of the exact test.
+struct UnitBox {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ inline UnitBox unit_box(const float4* __restrict__ ubox, long long u, int R) {
+    UnitBox b{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int k = 0; k < 4 * R; ++k) {
+        const float4 lo = __ldg(ubox + 2 * (u * 4 * R + k));
+        const float4 hi = __ldg(ubox + 2 * (u * 4 * R + k) + 1);
+        b.lx = fminf(b.lx, lo.x), b.ly = fminf(b.ly, lo.y), b.lz = fminf(b.lz, lo.z);
+        b.hx = fmaxf(b.hx, hi.x), b.hy = fmaxf(b.hy, hi.y), b.hz = fmaxf(b.hz, hi.z);
+    }
+    return b;
+}
+
+__device__ inline bool block_active(const UnitBox& b, const float4* __restrict__ tbox, int t) {
+    const float4 lo = __ldg(tbox + 2 * t), hi = __ldg(tbox + 2 * t + 1);
+    const float gx = fmaxf(0.0f, fmaxf(lo.x - b.hx, b.lx - hi.x));
+    const float gy = fmaxf(0.0f, fmaxf(lo.y - b.hy, b.ly - hi.y));
+    const float gz = fmaxf(0.0f, fmaxf(lo.z - b.hz, b.lz - hi.z));
+    const float lb2 = gx * gx + gy * gy + gz * gz;
+    return !(lb2 > lo.w * 1.0001f + 1e-3f);  // lo.w: max theta^2 of the tile
+}
+
+// Centre-point box and max theta^2 of each tile of `per` consecutive spatial centroids (an
+// empty tile never passes).
+__global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, int n_tiles,
+                           float4* __restrict__ tbox) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, -INFINITY);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+    for (int c = t * per; c < min(M, (t + 1) * per); ++c) {
+        const float4 v = ctr_sp[c];
+        lo.x = fminf(lo.x, v.x), lo.y = fminf(lo.y, v.y), lo.z = fminf(lo.z, v.z);
+        hi.x = fmaxf(hi.x, v.x), hi.y = fmaxf(hi.y, v.y), hi.z = fmaxf(hi.z, v.z);
+        lo.w = fmaxf(lo.w, v.w);
+    }
+    tbox[2 * t] = lo;
+    tbox[2 * t + 1] = hi;
+}
+
+// Spatial-order copies of the atlas for the GEMM modes.
+__global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float* cen_sp,
+                               float* thr2_sp, float4* ctr_sp) {
+    const int c = blockIdx.x * blockDim.y + threadIdx.y;
+    if (c >= at.M) return;
+    const int s = sp_s[c];
+    const float* src = at.cen + (size_t)s * CROW;
+    for (int k = threadIdx.x; k < CROW; k += blockDim.x) cen_sp[(size_t)c * CROW + k] = src[k];
+    if (threadIdx.x == 0) {
+        thr2_sp[c] = at.thr2[s];
+        ctr_sp[c] = make_float4(src[3 * CENTRE], src[3 * CENTRE + 1], src[3 * CENTRE + 2],
+                                at.thr2[s]);
+    }
+}
+
+// KE: K width of the operands in elements (64 for the directional columns, 32 for the
+// orientation-free ones). A row of KE elements is split into K regions of at most 128 bytes,
+// each loaded by its own TMA box and swizzled at its width (128 or 64 bytes).
+template <int FMT, int KE, int R, int N, int S, int ABUF>
 struct GemmCfg {
     static constexpr int ELEM = FMT == 1 ? 2 : 4;
-    static constexpr int KREG = FMT == 1 ? 1 : 2;             // 128-byte K regions per row
-    static constexpr int KSTEPS = FMT == 1 ? 4 : 8;           // MMA K steps (32 bytes each)
-    static constexpr int A_TILE = 128 * 64 * ELEM;            // one 128-row fiber tile
-    static constexpr int A_REGION = 128 * 128;                // bytes of one K region
-    static constexpr int B_TILE = N * 64 * ELEM;
-    static constexpr int B_REGION = N * 128;
-    static constexpr int ACC_COLS = R * N;                    // TMEM columns per accumulator
+    static constexpr int ROWB = KE * ELEM;                     // bytes of one operand row
+    static constexpr int REGB = ROWB < 128 ? ROWB : 128;       // bytes of a row in one region
+    static constexpr int KREG = ROWB / REGB;                   // K regions per row
+    static constexpr int KSTEPS = ROWB / 32;                   // MMA K steps (32 bytes each)
+    static constexpr int A_TILE = 128 * ROWB;                  // one 128-row fiber tile
+    static constexpr int A_REGION = 128 * REGB;                // bytes of one K region
+    static constexpr int B_TILE = N * ROWB;
+    static constexpr int B_REGION = N * REGB;
+    static constexpr int ACC_COLS = R * N;                     // TMEM columns per accumulator
+    static constexpr int NACC = 512 / ACC_COLS;                // accumulators in TMEM
     static constexpr int A_OFF = 0;
     static constexpr int B_OFF = A_OFF + ABUF * R * A_TILE;
     static constexpr int BAR_OFF = B_OFF + S * B_TILE;
-    static constexpr int NBAR = 2 * ABUF + 2 * S + 5;
+    static constexpr int NBAR = 2 * ABUF + 2 * S + 2 * NACC + 1;
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16 + 1024;  // + alignment slack
-    static_assert(2 * ACC_COLS <= 512, "two accumulators must fit TMEM");
+    static_assert(NACC >= 2 && NACC * ACC_COLS <= 512, "two or more accumulators in TMEM");
     static_assert(N % 32 == 0 && N >= 32 && N <= 256, "N");
+    static_assert(REGB == 128 || REGB == 64, "swizzle width");
     static_assert(A_TILE % 1024 == 0 && B_TILE % 1024 == 0, "1024-byte aligned tiles");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 struct Waiter {
@@ -452,11 +558,11 @@ struct SlotGrab {
     }
 };
 
-template <int FMT, int R, int N, int S, int ABUF>
+template <int FMT, int KE, int R, int N, int S, int ABUF>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               long long n_units, int n_tiles, int cols, GemmScratch g, unsigned* status) {
-    using C = GemmCfg<FMT, R, N, S, ABUF>;
+    using C = GemmCfg<FMT, KE, R, N, S, ABUF>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
@@ -465,8 +571,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint64_t* b_full = bars + 2 * ABUF;
     uint64_t* b_empty = bars + 2 * ABUF + S;
     uint64_t* acc_full = bars + 2 * ABUF + 2 * S;
-    uint64_t* acc_empty = acc_full + 2;
-    uint64_t* mma_done = acc_full + 4;
+    uint64_t* acc_empty = acc_full + C::NACC;
+    uint64_t* mma_done = acc_full + 2 * C::NACC;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
 
@@ -480,7 +586,7 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             mbar_init(b_full + i, 1);
             mbar_init(b_empty + i, 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < C::NACC; ++i) {
             mbar_init(acc_full + i, 1);
             mbar_init(acc_empty + i, EPI_WARPS);
         }
@@ -511,6 +617,7 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
             const int ab = ABUF == 2 ? (int)(it & 1) : 0;
             const long long use = ABUF == 2 ? (it >> 1) : it;  // uses of this A buffer so far
+            const UnitBox ub = unit_box(g.ubox, u, R);
             if (use > 0) ok = W.wait(a_empty + ab, (uint32_t)((use - 1) & 1));
             if (!ok) break;
             a_used |= 1u << ab;
@@ -519,9 +626,11 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             mbar_arrive_expect_tx(a_full + ab, (uint32_t)(R * C::A_TILE));
             for (int r = 0; r < R; ++r)
                 for (int kr = 0; kr < C::KREG; ++kr)
-                    tma_load_2d(sA + r * C::A_TILE + kr * C::A_REGION, &tmA, kr * 32,
+                    tma_load_2d(sA + r * C::A_TILE + kr * C::A_REGION, &tmA,
+                                kr * (C::REGB / C::ELEM),
                                 (int)((u * R + r) * 128), a_full + ab);
             for (int t = 0; t < n_tiles; ++t) {
+                if (!block_active(ub, g.tbox, t)) continue;
                 if (!W.wait(b_empty + stage, ((b_phase >> stage) & 1u) ^ 1u)) {
                     ok = false;
                     break;
@@ -531,7 +640,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 unsigned char* sB = smem + C::B_OFF + stage * C::B_TILE;
                 mbar_arrive_expect_tx(b_full + stage, (uint32_t)C::B_TILE);
                 for (int kr = 0; kr < C::KREG; ++kr)
-                    tma_load_2d(sB + kr * C::B_REGION, &tmB, kr * 32, t * N, b_full + stage);
+                    tma_load_2d(sB + kr * C::B_REGION, &tmB, kr * (C::REGB / C::ELEM), t * N,
+                                b_full + stage);
                 stage = stage + 1 == S ? 0 : stage + 1;
             }
         }
@@ -550,15 +660,19 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         uint32_t b_phase = 0;
         long long it = 0, tile = 0;
         bool ok = true;
+        long long active = 0;
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
             const int ab = ABUF == 2 ? (int)(it & 1) : 0;
             const long long use = ABUF == 2 ? (it >> 1) : it;
+            const UnitBox ub = unit_box(g.ubox, u, R);
             if (!W.wait(a_full + ab, (uint32_t)(use & 1))) break;
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + C::A_OFF + ab * R * C::A_TILE);
-            for (int t = 0; t < n_tiles; ++t, ++tile) {
-                const int cb = (int)(tile & 1);
-                const long long cuse = tile >> 1;
+            for (int t = 0; t < n_tiles; ++t) {
+                if (!block_active(ub, g.tbox, t)) continue;
+                ++active;
+                const int cb = (int)(tile % C::NACC);
+                const long long cuse = tile / C::NACC;
                 if (!W.wait(b_full + stage, (b_phase >> stage) & 1u)) {
                     ok = false;
                     break;
@@ -574,11 +688,12 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     const uint32_t d = tmem + (uint32_t)(cb * C::ACC_COLS + r * N);
 #pragma unroll
                     for (int kk = 0; kk < C::KSTEPS; ++kk) {
-                        const uint32_t koff = (kk / 4) * 0 + (uint32_t)((kk & 3) * 32);
-                        const uint64_t ad = make_sdesc_sw128(sA + r * C::A_TILE +
-                                                             (kk / 4) * C::A_REGION + koff);
-                        const uint64_t bd =
-                            make_sdesc_sw128(sB + (kk / 4) * C::B_REGION + koff);
+                        // K step kk starts 32 kk bytes into the row: region, then offset
+                        const int reg = (kk * 32) / C::REGB;
+                        const uint32_t koff = (uint32_t)((kk * 32) % C::REGB);
+                        const uint64_t ad = make_sdesc<C::REGB>(sA + r * C::A_TILE +
+                                                                reg * C::A_REGION + koff);
+                        const uint64_t bd = make_sdesc<C::REGB>(sB + reg * C::B_REGION + koff);
                         if (FMT == 1)
                             mma_f16(d, ad, bd, idesc, kk > 0);
                         else
@@ -588,9 +703,11 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 mma_commit(b_empty + stage);
                 mma_commit(acc_full + cb);
                 stage = stage + 1 == S ? 0 : stage + 1;
+                ++tile;
             }
             mma_commit(a_empty + ab);
         }
+        atomicAdd(g.cnt + 3, (unsigned long long)(active * R * 128 * N));
         // every MMA and every commit above has completed once this arrives
         mma_commit(mma_done);
         mbar_wait_bounded(mma_done, 0);
@@ -613,9 +730,11 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             for (int r = 0; r < 4; ++r)
                 al[r] = r < R ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane) : INFINITY;
             const unsigned fib0 = (unsigned)(u * R * 128 + 32 * q + lane);
-            for (int t = 0; t < n_tiles; ++t, ++tile) {
-                const int cb = (int)(tile & 1);
-                if (!W.wait(acc_full + cb, (uint32_t)((tile >> 1) & 1))) {
+            const UnitBox ub = unit_box(g.ubox, u, R);
+            for (int t = 0; t < n_tiles; ++t) {
+                if (!block_active(ub, g.tbox, t)) continue;
+                const int cb = (int)(tile % C::NACC);
+                if (!W.wait(acc_full + cb, (uint32_t)((tile / C::NACC) & 1))) {
                     ok = false;
                     break;
                 }
@@ -659,6 +778,7 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty + cb);
+                ++tile;
             }
         }
         __syncwarp();
@@ -758,6 +878,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
     __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
     __shared__ float s_cen[32 * EX_STRIDE];  // slot 64 of a row: theta^2 of its centroid
     __shared__ unsigned s_pre[32], s_msk[32], s_best[32];
+    __shared__ int s_sidx[32];               // sorted (bundle-major) index of each centroid row
     __shared__ unsigned s_q[EX_QCAP];        // fiber | bit << 5 | direct alive << 10 | rev << 11
     __shared__ float2 s_qm[EX_QCAP];         // partial maxima of the queued pairs
     __shared__ unsigned s_nq;
@@ -787,10 +908,13 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         for (int c = tid; c < 32 * (CROW / 4); c += EX_THREADS)
             cp_async16(s_fib + (c >> 4) * FS_STRIDE + 4 * (c & 15), fsrc + 4 * c);
         const int ncen = min(INV ? 32 : 16, at.M - (int)s0);
-        const float* csrc = at.cen + (size_t)s0 * CROW;
+        const float* csrc = g.cen_sp + (size_t)s0 * CROW;
         for (int c = tid; c < ncen * CROW; c += EX_THREADS)
             cp_async4(s_cen + (c >> 6) * EX_STRIDE + (c & 63), csrc + c);
-        if (tid < ncen) s_cen[tid * EX_STRIDE + 64] = __ldg(at.thr2 + s0 + tid);
+        if (tid < ncen) {
+            s_cen[tid * EX_STRIDE + 64] = __ldg(g.thr2_sp + s0 + tid);
+            s_sidx[tid] = __ldg(g.sp_s + s0 + tid);
+        }
         if (w == 0) {
             unsigned incl = __popc(m);
 #pragma unroll
@@ -883,7 +1007,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 d2 = md;
             }
             if (pass) {
-                atomicMin(g.key + h.x + lo, pack_key(d2, (int)s0 + j, o));
+                atomicMin(g.key + h.x + lo, pack_key(d2, s_sidx[j], o));
                 atomicMin(s_best + lo, __float_as_uint(d2));
             }
         }
@@ -918,6 +1042,7 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __rest
         stats[0] = pairs;
         stats[1] = (long long)g.cnt[2];
         stats[2] = (long long)g.cnt[1];
+        stats[3] = (long long)g.cnt[3];
     }
     if (f >= n) return;
     const unsigned long long k = g.key[f];
@@ -951,36 +1076,42 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// rows x 64 operand, K-major, 128-byte swizzle, box of box_rows rows and 128 bytes of K.
-bool make_tmap(CUtensorMap* m, const void* ptr, long long rows, int fmt, int box_rows) {
+// rows x ke operand, K-major, box of box_rows rows and one K region (128 bytes, swizzled at
+// 128, or a whole 64-byte row, swizzled at 64).
+bool make_tmap(CUtensorMap* m, const void* ptr, long long rows, int fmt, int ke, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int elem = fmt == 1 ? 2 : 4;
-    cuuint64_t dims[2] = {64, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(64 * elem)};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
+    const int regb = ke * elem < 128 ? ke * elem : 128;
+    cuuint64_t dims[2] = {(cuuint64_t)ke, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ke * elem)};
+    cuuint32_t box[2] = {(cuuint32_t)(regb / elem), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return fn(m, fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_TFLOAT32, 2,
               const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+              regb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 struct GemmShape {
-    int fmt, R, N, S, ABUF;
+    int fmt, ke, R, N, S, ABUF;
 };
 
-// Tile shapes per operand format; entry 0 is the default.
-const GemmShape kBf16Shapes[] = {{1, 4, 64, 6, 2}, {1, 2, 128, 4, 2}, {1, 1, 256, 3, 2}};
-const GemmShape kTf32Shapes[] = {{2, 2, 128, 2, 1}, {2, 4, 64, 4, 1}, {2, 1, 256, 2, 2}};
+// Tile shapes per mode; entry 0 is the default.
+// Narrower tiles leave room in TMEM for more accumulators (512 / (R N)), so the MMAs can run
+// further ahead of the epilogue.
+const GemmShape kDirBf16Shapes[] = {{1, 64, 1, 256, 3, 2}, {1, 64, 1, 128, 6, 2}, {1, 64, 1, 64, 8, 2}};
+const GemmShape kDirTf32Shapes[] = {{2, 64, 1, 256, 2, 2}, {2, 64, 1, 128, 4, 2}, {2, 64, 1, 64, 6, 2}};
+const GemmShape kInvBf16Shapes[] = {{1, 32, 1, 256, 6, 2}, {1, 32, 1, 128, 12, 2}, {1, 32, 1, 64, 16, 2}};
+const GemmShape kInvTf32Shapes[] = {{2, 32, 1, 256, 3, 2}, {2, 32, 1, 128, 8, 2}, {2, 32, 1, 64, 12, 2}};
 constexpr int kNumShapes = 3;
 
-template <int FMT, int R, int N, int S, int ABUF>
+template <int FMT, int KE, int R, int N, int S, int ABUF>
 cudaError_t launch_screen(const CUtensorMap& ta, const CUtensorMap& tb, long long n_units,
                           int n_tiles, int cols, const GemmScratch& g, unsigned* status, int sms,
                           cudaStream_t st) {
-    using C = GemmCfg<FMT, R, N, S, ABUF>;
-    auto kern = k_gemm_screen<FMT, R, N, S, ABUF>;
+    using C = GemmCfg<FMT, KE, R, N, S, ABUF>;
+    auto kern = k_gemm_screen<FMT, KE, R, N, S, ABUF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e) return e;
     const long long grid = n_units < sms ? n_units : sms;
@@ -991,16 +1122,22 @@ cudaError_t launch_screen(const CUtensorMap& ta, const CUtensorMap& tb, long lon
 cudaError_t dispatch_screen(const GemmShape& sh, const CUtensorMap& ta, const CUtensorMap& tb,
                             long long n_units, int n_tiles, int cols, const GemmScratch& g,
                             unsigned* status, int sms, cudaStream_t st) {
-#define SEG_SHAPE(F, R_, N_, S_, AB)                                                      \
-    if (sh.fmt == F && sh.R == R_ && sh.N == N_ && sh.S == S_ && sh.ABUF == AB)          \
-        return launch_screen<F, R_, N_, S_, AB>(ta, tb, n_units, n_tiles, cols, g, status, \
-                                                sms, st);
-    SEG_SHAPE(1, 4, 64, 6, 2)
-    SEG_SHAPE(1, 2, 128, 4, 2)
-    SEG_SHAPE(1, 1, 256, 3, 2)
-    SEG_SHAPE(2, 2, 128, 2, 1)
-    SEG_SHAPE(2, 4, 64, 4, 1)
-    SEG_SHAPE(2, 1, 256, 2, 2)
+#define SEG_SHAPE(F, KE, R_, N_, S_, AB)                                                     \
+    if (sh.fmt == F && sh.ke == KE && sh.R == R_ && sh.N == N_ && sh.S == S_ && sh.ABUF == AB) \
+        return launch_screen<F, KE, R_, N_, S_, AB>(ta, tb, n_units, n_tiles, cols, g, status, \
+                                                    sms, st);
+    SEG_SHAPE(1, 64, 1, 256, 3, 2)
+    SEG_SHAPE(1, 64, 1, 128, 6, 2)
+    SEG_SHAPE(1, 64, 1, 64, 8, 2)
+    SEG_SHAPE(2, 64, 1, 256, 2, 2)
+    SEG_SHAPE(2, 64, 1, 128, 4, 2)
+    SEG_SHAPE(2, 64, 1, 64, 6, 2)
+    SEG_SHAPE(1, 32, 1, 256, 6, 2)
+    SEG_SHAPE(1, 32, 1, 128, 12, 2)
+    SEG_SHAPE(1, 32, 1, 64, 16, 2)
+    SEG_SHAPE(2, 32, 1, 256, 3, 2)
+    SEG_SHAPE(2, 32, 1, 128, 8, 2)
+    SEG_SHAPE(2, 32, 1, 64, 12, 2)
 #undef SEG_SHAPE
     return cudaErrorInvalidValue;
 }
@@ -1011,28 +1148,40 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 int gemm_num_configs() { return kNumShapes; }
 
-seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st) {
+seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g,
+                           cudaStream_t st) {
     cudaError_t e;
-    if ((e = cudaMalloc(&g->stats, 3 * sizeof(long long))) ||
-        (e = cudaMemsetAsync(g->stats, 0, 3 * sizeof(long long), st)))
+    if ((e = cudaMalloc(&g->stats, 4 * sizeof(long long))) ||
+        (e = cudaMemsetAsync(g->stats, 0, 4 * sizeof(long long), st)))
         return cuda_fail(e, "gemm stats");
+    if ((e = cudaMalloc(&g->sp_s, (size_t)at.M * sizeof(int))) ||
+        (e = cudaMalloc(&g->cen_sp, (size_t)at.M * CROW * sizeof(float))) ||
+        (e = cudaMalloc(&g->thr2_sp, (size_t)at.M * sizeof(float))) ||
+        (e = cudaMalloc(&g->ctr_sp, (size_t)at.M * sizeof(float4))))
+        return cuda_fail(e, "gemm spatial order");
+    // the host array lives until the caller synchronizes the stream
+    if ((e = cudaMemcpyAsync(g->sp_s, sp_host, (size_t)at.M * sizeof(int), cudaMemcpyHostToDevice,
+                             st)))
+        return cuda_fail(e, "gemm spatial order");
+    k_prep_spatial<<<(at.M + 7) / 8, dim3(32, 8), 0, st>>>(at, g->sp_s, g->cen_sp, g->thr2_sp,
+                                                          g->ctr_sp);
     g->cols = 2 * at.M;
     g->cols_pad = (g->cols + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
     if ((e = cudaMalloc(&g->b_bf16, (size_t)g->cols_pad * 64 * 2)) ||
         (e = cudaMalloc(&g->b_tf32, (size_t)g->cols_pad * 64 * 4)))
         return cuda_fail(e, "gemm operands");
     const int threads = 128, blocks = (g->cols_pad + threads - 1) / threads;
-    k_prep_b<<<blocks, threads, 0, st>>>(at, 1, g->cols, g->cols_pad, g->b_bf16);
-    k_prep_b<<<blocks, threads, 0, st>>>(at, 2, g->cols, g->cols_pad, g->b_tf32);
+    k_prep_b<<<blocks, threads, 0, st>>>(at, g->sp_s, 1, g->cols, g->cols_pad, g->b_bf16);
+    k_prep_b<<<blocks, threads, 0, st>>>(at, g->sp_s, 2, g->cols, g->cols_pad, g->b_tf32);
     if ((e = cudaGetLastError())) return cuda_fail(e, "gemm operand prep");
     g->cols_inv = at.M;
     g->cols_inv_pad = (at.M + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
-    if ((e = cudaMalloc(&g->bi_bf16, (size_t)g->cols_inv_pad * 64 * 2)) ||
-        (e = cudaMalloc(&g->bi_tf32, (size_t)g->cols_inv_pad * 64 * 4)))
+    if ((e = cudaMalloc(&g->bi_bf16, (size_t)g->cols_inv_pad * KE_INV * 2)) ||
+        (e = cudaMalloc(&g->bi_tf32, (size_t)g->cols_inv_pad * KE_INV * 4)))
         return cuda_fail(e, "gemm operands");
     const int bi = (g->cols_inv_pad + threads - 1) / threads;
-    k_prep_b_inv<<<bi, threads, 0, st>>>(at, 1, g->cols_inv, g->cols_inv_pad, g->bi_bf16);
-    k_prep_b_inv<<<bi, threads, 0, st>>>(at, 2, g->cols_inv, g->cols_inv_pad, g->bi_tf32);
+    k_prep_b_inv<<<bi, threads, 0, st>>>(at, g->sp_s, 1, g->cols_inv, g->cols_inv_pad, g->bi_bf16);
+    k_prep_b_inv<<<bi, threads, 0, st>>>(at, g->sp_s, 2, g->cols_inv, g->cols_inv_pad, g->bi_tf32);
     if ((e = cudaGetLastError())) return cuda_fail(e, "gemm operand prep");
     return SEG_OK;
 }
@@ -1042,6 +1191,10 @@ void free_gemm_atlas(GemmAtlas* g) {
     cudaFree(g->b_tf32);
     cudaFree(g->bi_bf16);
     cudaFree(g->bi_tf32);
+    cudaFree(g->sp_s);
+    cudaFree(g->cen_sp);
+    cudaFree(g->thr2_sp);
+    cudaFree(g->ctr_sp);
     cudaFree(g->stats);
     *g = GemmAtlas{};
 }
@@ -1057,7 +1210,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const int cols_pad = inv ? ga->cols_inv_pad : ga->cols_pad;
     const void* bop = inv ? (tf32 ? ga->bi_tf32 : ga->bi_bf16) : (tf32 ? ga->b_tf32 : ga->b_bf16);
     if (config < 0 || config >= kNumShapes) config = 0;
-    const GemmShape sh = tf32 ? kTf32Shapes[config] : kBf16Shapes[config];
+    const GemmShape sh = inv ? (tf32 ? kInvTf32Shapes[config] : kInvBf16Shapes[config])
+                             : (tf32 ? kDirTf32Shapes[config] : kDirBf16Shapes[config]);
     const long long rows_per_unit = 128LL * sh.R;
     const long long n_units = (n + rows_per_unit - 1) / rows_per_unit;
     const long long n_pad = n_units * rows_per_unit;
@@ -1068,7 +1222,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     // per 32 fibers + slack (fibers past the room are rescanned exactly)
     const long long cap = n_pad / 32 * 16 + 65536;
     const size_t elem = tf32 ? 4 : 2;
-    const size_t off_alpha = align256((size_t)n_pad * 64 * elem);
+    const size_t off_alpha = align256((size_t)n_pad * sh.ke * elem);
     const size_t off_key = off_alpha + align256((size_t)n_pad * 4);
     const size_t off_flag = off_key + align256((size_t)n * 8);
     const size_t off_cnt = off_flag + align256((size_t)n);
@@ -1077,7 +1231,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const size_t off_hist = off_bin + align256((size_t)n * 4);
     const size_t off_top = off_hist + (size_t)NBINS * 4;
     const size_t off_fs = off_top + (size_t)NTOP * 4;
-    const size_t off_hdr = off_fs + (size_t)n_pad * CROW * 4;
+    const size_t off_ubox = off_fs + (size_t)n_pad * CROW * 4;
+    const size_t off_tbox = off_ubox + align256((size_t)(n_pad / 32) * 32);
+    const size_t off_hdr = off_tbox + align256((size_t)n_tiles * 32);
     const size_t off_mask = off_hdr + align256((size_t)cap * 8);
     const size_t bytes = off_mask + (size_t)cap * 128;
 
@@ -1104,11 +1260,19 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     unsigned* top = reinterpret_cast<unsigned*>(b8 + off_top);
     g.perm = perm;
     g.fs = reinterpret_cast<float*>(b8 + off_fs);
+    float4* ubox = reinterpret_cast<float4*>(b8 + off_ubox);
+    float4* tbox = reinterpret_cast<float4*>(b8 + off_tbox);
+    g.ubox = ubox;
+    g.tbox = tbox;
+    g.cen_sp = ga->cen_sp;
+    g.thr2_sp = ga->thr2_sp;
+    g.sp_s = ga->sp_s;
     g.cap = cap;
 
     cudaError_t e = cudaSuccess;
     CUtensorMap ta, tb;
-    if (!make_tmap(&ta, g.a, n_pad, fmt, 128) || !make_tmap(&tb, bop, cols_pad, fmt, sh.N)) {
+    if (!make_tmap(&ta, g.a, n_pad, fmt, sh.ke, 128) ||
+        !make_tmap(&tb, bop, cols_pad, fmt, sh.ke, sh.N)) {
         scratch_release(scratch, st);
         return fail(SEG_ERR_CUDA, "seg_label: cuTensorMapEncodeTiled failed");
     }
@@ -1127,8 +1291,17 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
-        k_prep_a<<<(unsigned)((n_pad + rows_per_block - 1) / rows_per_block), PREP_WARPS * 32, 0,
-                   st>>>(fib, perm, n, n_pad, at, fmt, inv ? 1 : 0, g.a, g.alpha, g.key, g.fs);
+        const unsigned pb = (unsigned)((n_pad + rows_per_block - 1) / rows_per_block);
+        auto prep = tf32 ? (inv ? k_prep_a<2, true> : k_prep_a<2, false>)
+                         : (inv ? k_prep_a<1, true> : k_prep_a<1, false>);
+        prep<<<pb, PREP_WARPS * 32, 0, st>>>(fib, perm, n, n_pad, at, g.a, g.alpha, g.key, g.fs,
+                                             ubox);
+        // centroids per column tile: N (orientation-free) or N / 2 (directional)
+        if (!e) e = cudaGetLastError();
+        if (!e)
+            k_tile_box<<<(n_tiles + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M,
+                                                             inv ? sh.N : sh.N / 2, n_tiles,
+                                                             tbox);
         e = cudaGetLastError();
     }
     if (!e) {

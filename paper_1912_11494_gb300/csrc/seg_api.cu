@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -210,6 +211,26 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
     for (int c = 0; c < M; ++c)
         for (int r = 0; r < 3; ++r) c0[r] += hc[(size_t)c * NC + 3 * CENTRE + r];
     for (int r = 0; r < 3; ++r) c0[r] = std::round(c0[r] / M);
+    // Spatial order of the sorted centroids for the tensor-core prune: Morton order of the 4 mm
+    // cell of the centre point (the grid the GEMM modes also sort fibers on), so that a tile of
+    // consecutive columns covers a compact region. sp[c] = sorted index at spatial position c.
+    std::vector<int32_t> sp(M);
+    {
+        std::vector<std::pair<uint32_t, int32_t>> key(M);
+        for (int s = 0; s < M; ++s) {
+            uint32_t k = 0;
+            for (int r = 0; r < 3; ++r) {
+                const double v = hc[(size_t)perm[s] * NC + 3 * CENTRE + r];
+                double t = std::floor((v - c0[r]) / 4.0) + 32.0;
+                const uint32_t cell = t < 0.0 ? 0u : t > 63.0 ? 63u : (uint32_t)t;
+                for (int b = 0; b < 6; ++b) k |= ((cell >> b) & 1u) << (3 * b + r);
+            }
+            key[s] = {k, s};
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const auto& x, const auto& y) { return x.first < y.first; });
+        for (int c = 0; c < M; ++c) sp[c] = key[c].second;
+    }
 
     seg_atlas* a = new seg_atlas();
     a->device = dev;
@@ -247,7 +268,7 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
     a->view.bundle = a->bundle;
     a->view.perm = a->perm;
     a->view.status = a->status;
-    seg_status s = prep_gemm_atlas(a->view, &a->gemm, st);
+    seg_status s = prep_gemm_atlas(a->view, sp.data(), &a->gemm, st);
     if (s != SEG_OK) {
         free_atlas(a);
         return s;
@@ -452,10 +473,10 @@ seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
 }
 
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
-                          int64_t* overflow_fibers) {
+                          int64_t* overflow_fibers, int64_t* screened) {
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_stats: atlas is NULL");
-    long long h[3] = {0, 0, 0};
+    long long h[4] = {0, 0, 0, 0};
     if (atlas->gemm.stats) {
         cudaError_t e = cudaMemcpy(h, atlas->gemm.stats, sizeof(h), cudaMemcpyDeviceToHost);
         if (e) return cuda_fail(e, "seg_gemm_stats");
@@ -463,6 +484,7 @@ seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survi
     if (pairs) *pairs = h[0];
     if (survivors) *survivors = h[1];
     if (overflow_fibers) *overflow_fibers = h[2];
+    if (screened) *screened = h[3];
     return SEG_OK;
 }
 

@@ -54,17 +54,25 @@ void free_scratch(ScratchArena* s);
 
 // Operands of the tensor-core prune (SEG_MODE_GEMM_*), built with the atlas.
 struct GemmAtlas {
-    int cols = 0;             // 2M columns: sorted centroid s direct at 2s, reversed at 2s+1
+    int cols = 0;             // 2M columns: centroid at spatial position c direct at 2c,
+                              // reversed at 2c+1
     int cols_pad = 0;         // cols rounded up to the N tile
     void* b_bf16 = nullptr;   // [cols_pad][64] bf16, centred, K-major
     void* b_tf32 = nullptr;   // [cols_pad][64] fp32 holding TF32-rounded values
-    int cols_inv = 0;         // M columns of orientation-free features (sorted centroid s at s)
+    int cols_inv = 0;         // M columns of orientation-free features (spatial position c at c)
     int cols_inv_pad = 0;
-    void* bi_bf16 = nullptr;  // [cols_inv_pad][64]
+    void* bi_bf16 = nullptr;  // [cols_inv_pad][32]
     void* bi_tf32 = nullptr;
-    long long* stats = nullptr;  // [3] pairs, survivors, overflow fibers of the last call
+    // Columns follow the spatial order of the centroids (Morton order of the centre point's
+    // 4 mm cell): spatial position c holds sorted centroid sp_s[c]; directional columns 2c, 2c+1.
+    int* sp_s = nullptr;      // [M]
+    float* cen_sp = nullptr;  // [M][64] centroid rows in spatial order
+    float* thr2_sp = nullptr; // [M] theta^2 in spatial order
+    float4* ctr_sp = nullptr; // [M] centre point and theta^2 in spatial order
+    long long* stats = nullptr;  // [4] pairs, survivors, overflow fibers, screened pairs
 };
-seg_status prep_gemm_atlas(const AtlasView& at, GemmAtlas* g, cudaStream_t st);
+seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g,
+                           cudaStream_t st);
 void free_gemm_atlas(GemmAtlas* g);
 int gemm_num_configs();
 seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,

@@ -80,14 +80,17 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-// Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t make_sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor, K-major, rows of ROWB = 128 or 64 bytes swizzled at their
+// width (the layout TMA writes with SWIZZLE_128B / SWIZZLE_64B): 8-row groups 8 x ROWB apart.
+template <int ROWB>
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
+    static_assert(ROWB == 128 || ROWB == 64, "swizzle width");
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
-    d |= (uint64_t)1u << 16;                         // leading byte offset (unused for SW128)
-    d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1u << 16;                         // leading byte offset (unused when swizzled)
+    d |= (uint64_t)((8u * ROWB) >> 4) << 32;         // stride byte offset: 8 rows
     d |= (uint64_t)1u << 46;                         // descriptor version for tcgen05
-    d |= (uint64_t)2u << 61;                         // 128-byte swizzle
+    d |= (uint64_t)(ROWB == 128 ? 2u : 4u) << 61;    // swizzle mode: 128-byte or 64-byte
     return d;
 }
 

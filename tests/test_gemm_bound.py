@@ -112,17 +112,20 @@ def test_margin_constants():
 
 
 def inv_features(x):
-    """33 orientation-free features per fiber: centre point, sqrt(2) x midpoints of (i, 20-i)."""
+    """30 orientation-free features per fiber: g = c / sqrt(2) + s_9, then sqrt(2) s_i for
+    i = 0..8, with c the centre point and s_i the midpoint of points i and 20 - i."""
     x = np.asarray(x, np.float32)
-    c = x[:, 10]
-    m = ((x[:, :10] + x[:, 20:10:-1]) * np.float32(0.70710678118654752)).astype(np.float32)
-    return np.concatenate([c, m.reshape(len(x), 30)], axis=1).astype(np.float32)
+    r2 = np.float32(0.70710678118654752)
+    g = (x[:, 10] * r2 + (x[:, 9] + x[:, 11]) * np.float32(0.5)).astype(np.float32)
+    m = ((x[:, :9] + x[:, 20:11:-1]) * r2).astype(np.float32)
+    return np.concatenate([g, m.reshape(len(x), 27)], axis=1).astype(np.float32)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "tf32"])
 def test_orientation_free_prune_never_drops_an_accepted_centroid(small_workload, fmt):
-    """I(a,b) = |dc|^2 + 2 sum |ds_i|^2 <= 21 d_ME^2 (both orientations), plus the same margin:
-    every centroid the exact test accepts in either orientation survives."""
+    """I'(a,b) = |dg|^2 + 2 sum_(i<9) |ds_i|^2 <= |dc|^2 + 2 sum_(i<10) |ds_i|^2 <= 21 d_ME^2
+    (both orientations), plus the same margin: every centroid the exact test accepts in either
+    orientation survives."""
     atlas, fib = small_workload
     order = np.argsort(atlas.bundle_of, kind="stable")
     cs = atlas.centroids[order]
@@ -149,7 +152,8 @@ def test_orientation_free_prune_never_drops_an_accepted_centroid(small_workload,
 
 
 def test_orientation_free_identity_is_a_lower_bound():
-    """The identity behind the features on random fibers: I <= min(S_direct, S_reversed)."""
+    """The inequalities behind the features on random fibers: I' <= min(S_direct, S_reversed),
+    and I' reaches that bound where it should: for a centroid equal to the fiber (both zero)."""
     rng = np.random.default_rng(2)
     A = rng.normal(0, 20, size=(30, 21, 3)).astype(np.float32)
     B = rng.normal(0, 20, size=(40, 21, 3)).astype(np.float32)
@@ -158,3 +162,6 @@ def test_orientation_free_identity_is_a_lower_bound():
     Sd = ((A[:, None].astype(np.float64) - B[None]) ** 2).sum((-1, -2))
     Sr = ((A[:, None].astype(np.float64) - B[None, :, ::-1]) ** 2).sum((-1, -2))
     assert np.all(I <= np.minimum(Sd, Sr) * (1 + 1e-6) + 1e-6)
+    FA2 = inv_features(A[:, ::-1]).astype(np.float64)  # the features ignore the orientation
+    np.testing.assert_allclose(FA2, FA, rtol=1e-6, atol=1e-4)
+    assert np.all(((FA[:, None] - FA[None]) ** 2).sum(-1).diagonal() == 0)
