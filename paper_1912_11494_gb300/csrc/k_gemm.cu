@@ -22,7 +22,7 @@
 // order. The screen is a persistent CTA per SM, warp-specialised: warp 0 issues TMA loads (R
 // fiber tiles of 128 rows per work unit, double-buffered, and a ring of S centroid tiles of N
 // columns), warp 1 issues tcgen05.mma (M=128, N, K) into one of 512/(R*N) TMEM accumulators of R*N
-// columns, and eight epilogue warps read the other accumulator with tcgen05.ld.red, which
+// columns, and eight epilogue warps read a finished accumulator with tcgen05.ld.red, which
 // returns each row's max over 32 columns: only when that max reaches alpha in some row does the
 // warp compare the individual values and write a block record (32 fibers x 32 columns, one
 // column mask per fiber). A second kernel runs the exact test of Section 2.3 on every survivor
@@ -54,9 +54,10 @@ namespace seg {
 namespace {
 
 constexpr int EPI_WARPS = 8;       // two epilogue warps per TMEM lane quarter
+constexpr int EPI_SUB = EPI_WARPS / 4;
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA, then epilogue
 constexpr int COL_ALIGN = 256;     // columns padded to a multiple of this
-constexpr int SLOT_GRAB = 16;      // block records an epilogue warp reserves at a time
+constexpr int SLOT_GRAB = 64;      // block records an epilogue warp reserves at a time
 constexpr unsigned EMPTY_SLOT = 0xFFFFFFFFu;  // header of a reserved record left unused
 constexpr unsigned long long NAN_KEY = ~0ull - 1ull;
 constexpr float PAD_NEG = -1e30f;  // pad of padding columns: never survives
@@ -85,8 +86,9 @@ struct GemmScratch {
     float* alpha;                 // [n_pad] (sorted order, as key and flag)
     unsigned long long* key;      // [n]
     unsigned char* flag;          // [n] survivors dropped for lack of list space
-    const float4* ubox;           // [n_pad / 32][2] centre-point box of 32 sorted fibers
-    const float4* tbox;           // [n_tiles][2] centre-point box of a column tile, max theta^2
+    const unsigned long long* amask;  // [n_units][awords] bit t: the unit's block with tile t
+                                      // is computed (the others are culled)
+    int awords;
     const float* cen_sp;          // the atlas's spatial-order arrays (GemmAtlas)
     const float* thr2_sp;
     const int* sp_s;
@@ -310,7 +312,7 @@ __global__ void k_bin_scatter(const unsigned* __restrict__ bin, long long n,
 
 // Fiber rows in sorted order: centred coordinates (or the orientation-free features), 1 in
 // the pad column, alpha_i; keys initialised. One warp per 32 rows: the rows perm[r0 .. r0+31]
-// are gathered with two coalesced loads each into shared memory, each lane converts one row,
+// are copied (cp.async, all in flight together) into shared memory, each lane converts one row,
 // and the 32 output rows go back out with coalesced stores.
 //
 // |p|^2 is summed in FP32 (fmaf, fixed order): the computed value is within 63 u_32 |p|^2 of the
@@ -332,12 +334,12 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
     const int rows_in = (int)max(0LL, min(32LL, n - r0));
     float* si = reinterpret_cast<float*>(s_buf[w]);
     const unsigned src_row = lane < rows_in ? __ldg(perm + r0 + lane) : 0u;
-#pragma unroll 4
-    for (int r = 0; r < rows_in; ++r) {
+    for (int r = 0; r < rows_in; ++r) {  // all 63 x 32 copies in flight at once
         const float* src = fib + (size_t)__shfl_sync(0xffffffffu, src_row, r) * NC;
-        si[r * PREP_STRIDE + lane] = __ldg(src + lane);
-        if (lane < NC - 32) si[r * PREP_STRIDE + 32 + lane] = __ldg(src + 32 + lane);
+        cp_async4(si + r * PREP_STRIDE + lane, src + lane);
+        if (lane < NC - 32) cp_async4(si + r * PREP_STRIDE + 32 + lane, src + 32 + lane);
     }
+    cp_async_wait_all();
     __syncwarp();
     // the sorted copy of the rows (read by the exact re-check)
     float* fdst = fs + r0 * CROW;
@@ -448,6 +450,38 @@ __device__ inline bool block_active(const UnitBox& b, const float4* __restrict__
     const float gz = fmaxf(0.0f, fmaxf(lo.z - b.hz, b.lz - hi.z));
     const float lb2 = gx * gx + gy * gy + gz * gz;
     return !(lb2 > lo.w * 1.0001f + 1e-3f);  // lo.w: max theta^2 of the tile
+}
+
+constexpr int MAXW = 8;  // mask words per unit: at most 512 column tiles
+
+struct UnitMask {
+    unsigned long long w[MAXW];
+    __device__ void load(const GemmScratch& g, long long u, long long n_units) {
+#pragma unroll
+        for (int k = 0; k < MAXW; ++k)
+            w[k] = (u < n_units && k < g.awords) ? __ldg(g.amask + u * g.awords + k) : 0ull;
+    }
+    __device__ bool any() const {
+        unsigned long long a = 0;
+#pragma unroll
+        for (int k = 0; k < MAXW; ++k) a |= w[k];
+        return a != 0;
+    }
+};
+
+// Active-block masks: one thread per work unit of R x 128 sorted fibers, one bit per tile.
+__global__ void k_block_mask(const float4* __restrict__ ubox, const float4* __restrict__ tbox,
+                             long long n_units, int R, int n_tiles, int words,
+                             unsigned long long* __restrict__ amask) {
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_units) return;
+    const UnitBox b = unit_box(ubox, u, R);
+    for (int wd = 0; wd < words; ++wd) {
+        unsigned long long m = 0;
+        for (int k = 0; k < 64 && wd * 64 + k < n_tiles; ++k)
+            if (block_active(b, tbox, wd * 64 + k)) m |= 1ull << k;
+        amask[u * words + wd] = m;
+    }
 }
 
 // Centre-point box and max theta^2 of each tile of `per` consecutive spatial centroids (an
@@ -614,10 +648,16 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         uint32_t a_used = 0, a_par = 0;
         long long it = 0;
         bool ok = true;
-        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+        UnitMask um, nm;
+        um.load(g, blockIdx.x, n_units);
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            nm.load(g, u + gridDim.x, n_units);  // next unit's mask, loaded ahead
+            if (!um.any()) {                      // every block of the unit is culled
+                um = nm;
+                continue;
+            }
             const int ab = ABUF == 2 ? (int)(it & 1) : 0;
             const long long use = ABUF == 2 ? (it >> 1) : it;  // uses of this A buffer so far
-            const UnitBox ub = unit_box(g.ubox, u, R);
             if (use > 0) ok = W.wait(a_empty + ab, (uint32_t)((use - 1) & 1));
             if (!ok) break;
             a_used |= 1u << ab;
@@ -629,8 +669,10 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     tma_load_2d(sA + r * C::A_TILE + kr * C::A_REGION, &tmA,
                                 kr * (C::REGB / C::ELEM),
                                 (int)((u * R + r) * 128), a_full + ab);
-            for (int t = 0; t < n_tiles; ++t) {
-                if (!block_active(ub, g.tbox, t)) continue;
+#pragma unroll 1
+            for (int wd = 0; wd < MAXW && ok; ++wd)
+            for (unsigned long long bits = um.w[wd]; bits; bits &= bits - 1) {
+                const int t = wd * 64 + __ffsll((long long)bits) - 1;
                 if (!W.wait(b_empty + stage, ((b_phase >> stage) & 1u) ^ 1u)) {
                     ok = false;
                     break;
@@ -644,6 +686,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 b_full + stage);
                 stage = stage + 1 == S ? 0 : stage + 1;
             }
+            ++it;
+            um = nm;
         }
         if (s_abort) {
             // copies this thread issued may still be landing: wait for each buffer's last load
@@ -661,15 +705,22 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         long long it = 0, tile = 0;
         bool ok = true;
         long long active = 0;
-        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+        UnitMask um, nm;
+        um.load(g, blockIdx.x, n_units);
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            nm.load(g, u + gridDim.x, n_units);
+            if (!um.any()) {
+                um = nm;
+                continue;
+            }
             const int ab = ABUF == 2 ? (int)(it & 1) : 0;
             const long long use = ABUF == 2 ? (it >> 1) : it;
-            const UnitBox ub = unit_box(g.ubox, u, R);
             if (!W.wait(a_full + ab, (uint32_t)(use & 1))) break;
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + C::A_OFF + ab * R * C::A_TILE);
-            for (int t = 0; t < n_tiles; ++t) {
-                if (!block_active(ub, g.tbox, t)) continue;
+#pragma unroll 1
+            for (int wd = 0; wd < MAXW && ok; ++wd)
+            for (unsigned long long bits = um.w[wd]; bits; bits &= bits - 1) {
                 ++active;
                 const int cb = (int)(tile % C::NACC);
                 const long long cuse = tile / C::NACC;
@@ -706,6 +757,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 ++tile;
             }
             mma_commit(a_empty + ab);
+            ++it;
+            um = nm;
         }
         atomicAdd(g.cnt + 3, (unsigned long long)(active * R * 128 * N));
         // every MMA and every commit above has completed once this arrives
@@ -713,13 +766,13 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         mbar_wait_bounded(mma_done, 0);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
-        // Warp w reads TMEM lane quarter w % 4 (the hardware's rule) and, with its partner
-        // warp of the same quarter, half of the 32-column chunks of each accumulator. Two
-        // tcgen05.ld.red are in flight per wait.
+        // Warp w reads TMEM lane quarter w % 4 (the hardware's rule) and, with the other
+        // EPI_SUB - 1 warps of the same quarter, a share of the 32-column chunks of each
+        // accumulator. Two tcgen05.ld.red are in flight per wait.
         constexpr int CPR = N / 32;               // chunks per fiber tile row block
         constexpr int CHUNKS = R * CPR;           // chunks per accumulator
         const int q = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int sub = (warp - 2) >> 2;  // which of the quarter's EPI_SUB warps
         SlotGrab slots;
         unsigned long long surv = 0;
         long long tile = 0;
@@ -730,9 +783,10 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             for (int r = 0; r < 4; ++r)
                 al[r] = r < R ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane) : INFINITY;
             const unsigned fib0 = (unsigned)(u * R * 128 + 32 * q + lane);
-            const UnitBox ub = unit_box(g.ubox, u, R);
-            for (int t = 0; t < n_tiles; ++t) {
-                if (!block_active(ub, g.tbox, t)) continue;
+            for (int wd = 0; wd < g.awords && ok; ++wd)
+            for (unsigned long long bits = __ldg(g.amask + u * g.awords + wd); bits;
+                 bits &= bits - 1) {
+                const int t = wd * 64 + __ffsll((long long)bits) - 1;
                 const int cb = (int)(tile % C::NACC);
                 if (!W.wait(acc_full + cb, (uint32_t)((tile / C::NACC) & 1))) {
                     ok = false;
@@ -741,16 +795,16 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cb * C::ACC_COLS);
 #pragma unroll 1
-                for (int c0 = half; c0 < CHUNKS; c0 += 4) {
+                for (int c0 = sub; c0 < CHUNKS; c0 += 2 * EPI_SUB) {
                     float v[2][32], mx[2];
                     tmem_ld_red32(tbase + (uint32_t)(32 * c0), v[0], mx[0]);
-                    const bool two = c0 + 2 < CHUNKS;
-                    if (two) tmem_ld_red32(tbase + (uint32_t)(32 * (c0 + 2)), v[1], mx[1]);
+                    const bool two = c0 + EPI_SUB < CHUNKS;
+                    if (two) tmem_ld_red32(tbase + (uint32_t)(32 * (c0 + EPI_SUB)), v[1], mx[1]);
                     tmem_wait_ld();
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if (h == 1 && !two) break;
-                        const int c = c0 + 2 * h;
+                        const int c = c0 + EPI_SUB * h;
                         const int r = c / CPR;
                         const float a = r == 0 ? al[0] : r == 1 ? al[1] : r == 2 ? al[2] : al[3];
                         if (!__any_sync(0xffffffffu, mx[h] >= a)) continue;
@@ -837,18 +891,6 @@ constexpr int EX_STRIDE = 65;    // padded centroid row in shared memory: lanes 
                                  // rows never share a bank
 constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
-
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
 // Stages of the exact test in orientation O (0: points in order, 1: reversed as in Eq. 2).
 template <int O>
@@ -1218,6 +1260,11 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const int n_tiles = cols_pad / sh.N;
     if (n_pad >= (1LL << 32))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
+    const int awords = (n_tiles + 63) / 64;
+    if (awords > MAXW)
+        return fail(SEG_ERR_UNSUPPORTED,
+                    "seg_label: %d column tiles of %d exceed the GEMM modes' limit of %d", n_tiles,
+                    sh.N, 64 * MAXW);
     // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for 16
     // per 32 fibers + slack (fibers past the room are rescanned exactly)
     const long long cap = n_pad / 32 * 16 + 65536;
@@ -1233,7 +1280,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const size_t off_fs = off_top + (size_t)NTOP * 4;
     const size_t off_ubox = off_fs + (size_t)n_pad * CROW * 4;
     const size_t off_tbox = off_ubox + align256((size_t)(n_pad / 32) * 32);
-    const size_t off_hdr = off_tbox + align256((size_t)n_tiles * 32);
+    const size_t off_amask = off_tbox + align256((size_t)n_tiles * 32);
+    const size_t off_hdr = off_amask + align256((size_t)n_units * awords * 8);
     const size_t off_mask = off_hdr + align256((size_t)cap * 8);
     const size_t bytes = off_mask + (size_t)cap * 128;
 
@@ -1262,8 +1310,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     g.fs = reinterpret_cast<float*>(b8 + off_fs);
     float4* ubox = reinterpret_cast<float4*>(b8 + off_ubox);
     float4* tbox = reinterpret_cast<float4*>(b8 + off_tbox);
-    g.ubox = ubox;
-    g.tbox = tbox;
+    g.amask = reinterpret_cast<unsigned long long*>(b8 + off_amask);
+    g.awords = awords;
     g.cen_sp = ga->cen_sp;
     g.thr2_sp = ga->thr2_sp;
     g.sp_s = ga->sp_s;
@@ -1302,6 +1350,10 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
             k_tile_box<<<(n_tiles + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M,
                                                              inv ? sh.N : sh.N / 2, n_tiles,
                                                              tbox);
+        if (!e)
+            k_block_mask<<<(unsigned)((n_units + 127) / 128), 128, 0, st>>>(
+                ubox, tbox, n_units, sh.R, n_tiles, awords,
+                reinterpret_cast<unsigned long long*>(b8 + off_amask));
         e = cudaGetLastError();
     }
     if (!e) {
