@@ -880,10 +880,13 @@ __device__ inline bool exact_one(const float* a, const float* b, float bound2, f
 // Exact test of the survivors, one block record per CTA at a time. The CTA copies (cp.async) the
 // block's 32 fiber rows (contiguous in the sorted copy) and the chunk's centroid rows into shared
 // memory, with theta^2 beside each centroid and each fiber's best d^2 so far; the next record's
-// header and masks are loaded while the current one is tested. The block's (fiber, column) pairs are numbered by a prefix sum of
-// the mask popcounts. Phase A runs test1 and test2 (Section 2.3) on every pair and queues the
+// header and masks are loaded while the current one is tested. Warp 0 lists the block's
+// (fiber, column) pairs in shared memory (a prefix sum of the mask popcounts places each fiber's
+// pairs). Phase A runs test1 and test2 (Section 2.3) on every pair and queues the
 // pairs with a live orientation; phase B runs test3 and test4 on the queue, so that the lanes of
-// a warp do the same stage of the test. The bound is min(theta^2, the fiber's best so far);
+// a warp do the same stage of the test: first each fiber's queued pair with the smallest partial
+// maximum (usually its best), then the rest, most of which the tightened bound now discards
+// early. The bound is min(theta^2, the fiber's best so far);
 // exits are strict (> bound), so equal distances still reach the atomicMin of the packed key and
 // the tie rule of Algorithm 1 holds.
 constexpr int EX_THREADS = 128;
@@ -914,16 +917,58 @@ __device__ __forceinline__ float rest17(const float* a, const float* b, float m)
     return m;
 }
 
+constexpr unsigned DONE_ENTRY = 0xFFFFFFFFu;  // queue entry already tested
+
+// test3 and test4 of one queued pair (its live orientations and partial maxima from phase A),
+// against min(theta^2, the fiber's best so far); a pass is merged into the fiber's packed key
+// and its best. A tighter bound than phase A's discards only pairs strictly worse than a pair
+// already merged.
+template <bool INV>
+__device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float* s_fib,
+                                            const float* s_cen, const int* s_sidx,
+                                            unsigned* s_best, unsigned long long* key) {
+    const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
+    const int j = INV ? bit : bit >> 1;
+    const float* a = s_fib + lo * FS_STRIDE;
+    const float* b = s_cen + j * EX_STRIDE;
+    const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
+    float md = mm.x, mr = mm.y, d2;
+    int o;
+    bool pass;
+    if (INV) {
+        bool ad = ((ent >> 10) & 1u) && md <= bound;
+        bool ar = ((ent >> 11) & 1u) && mr <= bound;
+        if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; }
+        if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; }
+        if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; }
+        if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; }
+        pass = ad || ar;
+        if (ad && (!ar || md <= mr)) { d2 = md; o = 0; } else { d2 = mr; o = 1; }
+    } else {
+        o = bit & 1;
+        pass = md <= bound;
+        if (pass) { md = o ? mid4<1>(a, b, md) : mid4<0>(a, b, md); pass = md <= bound; }
+        if (pass) { md = o ? rest17<1>(a, b, md) : rest17<0>(a, b, md); pass = md <= bound; }
+        d2 = md;
+    }
+    if (pass) {
+        atomicMin(key + lo, pack_key(d2, s_sidx[j], o));
+        atomicMin(s_best + lo, __float_as_uint(d2));
+    }
+}
+
 template <bool INV>
 __global__ void __launch_bounds__(EX_THREADS)
 k_exact_blocks(AtlasView at, GemmScratch g) {
     __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
     __shared__ float s_cen[32 * EX_STRIDE];  // slot 64 of a row: theta^2 of its centroid
-    __shared__ unsigned s_pre[32], s_msk[32], s_best[32];
+    __shared__ unsigned s_pre[32], s_best[32];
     __shared__ int s_sidx[32];               // sorted (bundle-major) index of each centroid row
     __shared__ unsigned s_q[EX_QCAP];        // fiber | bit << 5 | direct alive << 10 | rev << 11
     __shared__ float2 s_qm[EX_QCAP];         // partial maxima of the queued pairs
     __shared__ unsigned s_nq;
+    __shared__ unsigned long long s_first[32];  // per fiber: partial max bits << 32 | queue index
+    __shared__ unsigned short s_pair[EX_QCAP];  // the block's pairs: fiber | bit << 5
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const long long cnt = min((long long)*g.cnt, g.cap);
@@ -965,8 +1010,12 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 if (lane >= off) incl += v;
             }
             s_pre[lane] = incl;
-            s_msk[lane] = m;
+            // this fiber's pairs, numbered after the previous fibers'
+            unsigned k = incl - __popc(m);
+            for (unsigned mm = m; mm; mm &= mm - 1, ++k)
+                s_pair[k] = (unsigned short)(lane | ((__ffs(mm) - 1) << 5));
             s_best[lane] = m ? (unsigned)(g.key[h.x + lane] >> 32) : 0xFFFFFFFFu;
+            s_first[lane] = ~0ull;
             if (lane == 0) s_nq = 0;
         }
         cp_async_wait_all();
@@ -979,13 +1028,8 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             unsigned ent = 0;
             float md = 0.0f, mr = 0.0f;
             if (p < total) {
-                int lo = 0, hi = 31;  // first fiber whose inclusive prefix exceeds p
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_pre[mid] > p) hi = mid; else lo = mid + 1;
-                }
-                const unsigned prev = lo ? s_pre[lo - 1] : 0u;
-                const int bit = (int)__fns(s_msk[lo], 0u, (int)(p - prev) + 1);
+                const unsigned pr = s_pair[p];
+                const int lo = (int)(pr & 31u), bit = (int)(pr >> 5);
                 const float* a = s_fib + lo * FS_STRIDE;
                 const float* b = s_cen + (INV ? bit : bit >> 1) * EX_STRIDE;
                 const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
@@ -1014,44 +1058,31 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 const unsigned q = base + __popc(bal & lt);
                 s_q[q] = ent;
                 s_qm[q] = make_float2(md, mr);
+                // the fiber's most promising pair: smallest partial maximum of a live
+                // orientation (non-negative floats order as their bit patterns)
+                const float pm = (ent >> 10) & 1u ? ((ent >> 11) & 1u ? fminf(md, mr) : md) : mr;
+                atomicMin(s_first + (ent & 31u),
+                          ((unsigned long long)__float_as_uint(pm) << 32) | q);
             }
         }
         __syncthreads();
-        // phase B: test3 and test4 on the queued pairs
+        // the next record's fiber rows into L2 while this one is tested (its header has
+        // arrived by now)
+        if (tid < 64 && hn.x != EMPTY_SLOT && blk + gridDim.x < cnt)
+            prefetch_l2(g.fs + (size_t)hn.x * CROW + tid * 32);
+        // phase B1: each fiber's most promising pair first, so that the others meet a tight
+        // bound; phase B2: the rest of the queue
+        if (tid < 32 && s_first[tid] != ~0ull) {
+            const unsigned q = (unsigned)s_first[tid];
+            exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x);
+            s_q[q] = DONE_ENTRY;
+        }
+        __syncthreads();
         const unsigned nq = s_nq;
         for (unsigned q = tid; q < nq; q += EX_THREADS) {
             const unsigned ent = s_q[q];
-            const float2 mm = s_qm[q];
-            const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
-            const int j = INV ? bit : bit >> 1;
-            const float* a = s_fib + lo * FS_STRIDE;
-            const float* b = s_cen + j * EX_STRIDE;
-            // the best may have improved since phase A: a tighter bound discards only pairs
-            // that are strictly worse than a pair already merged
-            const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
-            float md = mm.x, mr = mm.y, d2;
-            int o;
-            bool pass;
-            if (INV) {
-                bool ad = ((ent >> 10) & 1u) && md <= bound;
-                bool ar = ((ent >> 11) & 1u) && mr <= bound;
-                if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; }
-                if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; }
-                if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; }
-                if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; }
-                pass = ad || ar;
-                if (ad && (!ar || md <= mr)) { d2 = md; o = 0; } else { d2 = mr; o = 1; }
-            } else {
-                o = bit & 1;
-                pass = md <= bound;
-                if (pass) { md = o ? mid4<1>(a, b, md) : mid4<0>(a, b, md); pass = md <= bound; }
-                if (pass) { md = o ? rest17<1>(a, b, md) : rest17<0>(a, b, md); pass = md <= bound; }
-                d2 = md;
-            }
-            if (pass) {
-                atomicMin(g.key + h.x + lo, pack_key(d2, s_sidx[j], o));
-                atomicMin(s_best + lo, __float_as_uint(d2));
-            }
+            if (ent != DONE_ENTRY)
+                exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x);
         }
         __syncthreads();  // the buffers are refilled for the next record
     }
