@@ -894,6 +894,7 @@ constexpr int EX_STRIDE = 65;    // padded centroid row in shared memory: lanes 
                                  // rows never share a bank
 constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
+constexpr int EX_RUN = 16;       // consecutive records a CTA takes at a time
 
 // Stages of the exact test in orientation O (0: points in order, 1: reversed as in Eq. 2).
 template <int O>
@@ -972,28 +973,45 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const long long cnt = min((long long)*g.cnt, g.cap);
-    long long blk = blockIdx.x;
+    __shared__ long long s_run;
+    // Records are taken in runs of EX_RUN consecutive ones: an epilogue warp writes its records
+    // for the same 32 fibers one after another, so consecutive records usually share their
+    // fiber rows (kept in shared memory) and each fiber's best so far.
+    long long blk = 0, blk_end = 0;
+    unsigned cur = EMPTY_SLOT;  // first fiber of the rows in s_fib
     uint2 hn = make_uint2(EMPTY_SLOT, 0u);  // the next record's header and masks, loaded one
     unsigned mn = 0u;                       // record ahead
-    if (blk < cnt) {
-        hn = g.hdr[blk];
-        mn = g.mask[blk * 32 + lane];
-    }
-    for (; blk < cnt; blk += gridDim.x) {
+    for (;;) {
+        if (blk == blk_end) {
+            __syncthreads();
+            if (tid == 0) s_run = (long long)atomicAdd(g.cnt + 4, (unsigned long long)EX_RUN);
+            __syncthreads();
+            blk = s_run;
+            if (blk >= cnt) break;
+            blk_end = min(blk + EX_RUN, cnt);
+            hn = g.hdr[blk];
+            mn = g.mask[blk * 32 + lane];
+        }
         const uint2 h = hn;
         const unsigned m = mn;
-        if (blk + gridDim.x < cnt) {
-            hn = g.hdr[blk + gridDim.x];
-            mn = g.mask[(blk + gridDim.x) * 32 + lane];
+        ++blk;
+        if (blk < blk_end) {
+            hn = g.hdr[blk];
+            mn = g.mask[blk * 32 + lane];
         }
         if (h.x == EMPTY_SLOT) continue;
         const unsigned s0 = INV ? h.y : h.y >> 1;
-        // the 32 sorted fiber rows (16-byte copies) and the chunk's centroid rows (4-byte
-        // copies into conflict-free rows), theta^2 beside each centroid
+        const bool same = h.x == cur;
+        // the 32 sorted fiber rows (16-byte copies; kept from the previous record when it had
+        // the same fibers) and the chunk's centroid rows (4-byte copies into conflict-free
+        // rows), theta^2 beside each centroid
         const float* fsrc = g.fs + (size_t)h.x * CROW;
+        if (!same) {
 #pragma unroll
-        for (int c = tid; c < 32 * (CROW / 4); c += EX_THREADS)
-            cp_async16(s_fib + (c >> 4) * FS_STRIDE + 4 * (c & 15), fsrc + 4 * c);
+            for (int c = tid; c < 32 * (CROW / 4); c += EX_THREADS)
+                cp_async16(s_fib + (c >> 4) * FS_STRIDE + 4 * (c & 15), fsrc + 4 * c);
+        }
+        cur = h.x;
         const int ncen = min(INV ? 32 : 16, at.M - (int)s0);
         const float* csrc = g.cen_sp + (size_t)s0 * CROW;
         for (int c = tid; c < ncen * CROW; c += EX_THREADS)
@@ -1014,7 +1032,8 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             unsigned k = incl - __popc(m);
             for (unsigned mm = m; mm; mm &= mm - 1, ++k)
                 s_pair[k] = (unsigned short)(lane | ((__ffs(mm) - 1) << 5));
-            s_best[lane] = m ? (unsigned)(g.key[h.x + lane] >> 32) : 0xFFFFFFFFu;
+            const unsigned kb = (unsigned)(g.key[h.x + lane] >> 32);
+            s_best[lane] = same ? min(s_best[lane], kb) : kb;
             s_first[lane] = ~0ull;
             if (lane == 0) s_nq = 0;
         }
@@ -1066,10 +1085,6 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             }
         }
         __syncthreads();
-        // the next record's fiber rows into L2 while this one is tested (its header has
-        // arrived by now)
-        if (tid < 64 && hn.x != EMPTY_SLOT && blk + gridDim.x < cnt)
-            prefetch_l2(g.fs + (size_t)hn.x * CROW + tid * 32);
         // phase B1: each fiber's most promising pair first, so that the others meet a tight
         // bound; phase B2: the rest of the queue
         if (tid < 32 && s_first[tid] != ~0ull) {
