@@ -5,8 +5,12 @@ One step labels the whole synthetic subject (4,145,000 fibers of 21 points, the 
 subject size) against a 500-bundle x 20-centroid atlas through the C ABI, with inputs resident
 in HBM (1.04 GB of fibers, larger than L2). Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode plain|gemm_bf16|gemm_tf32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode best|plain|gemm_bf16|gemm_tf32|
+                  gemm_inv_bf16|gemm_inv_tf32] [--config C] [--n N] [--workload batch16]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+--mode best (the default) tunes and times every mode and reports the fastest as the headline,
+with every mode's time, per-kernel event timings and rooflines in "modes" / "rooflines".
 
 Multi-GPU: one process per GPU (torchrun); every rank labels its own full subject (weak
 scaling, no data-path collective); the time is the max over ranks.
@@ -206,11 +210,16 @@ def _has_cuda():
 
 # ----------------------------------------------------------------------------- our arm
 MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32")
-DOMINANT = {"plain": "plain", "gemm_bf16": "gemm_screen", "gemm_tf32": "gemm_screen",
-            "gemm_inv_bf16": "gemm_screen", "gemm_inv_tf32": "gemm_screen"}
-KERNEL_NAME = {"plain": "k_label_plain", "gemm_screen": "k_gemm_screen"}
-LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
+KERNEL_NAME = {"plain": "k_label_plain", "gemm_screen": "k_gemm_screen",
+               "gemm_exact": "k_exact_blocks", "gemm_prep": "k_prep_a",
+               "gemm_sort": "k_bin_count", "gemm_finalize": "k_finalize"}
+LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact",
                 "gemm_finalize")
+# kernels the library launches inside each profiled scope (the sort is a count, two scans and a
+# scatter; the prep scope holds the fiber operand, the tile boxes and the active-block masks;
+# the finalize scope the overflow rescan and the label write)
+KERNELS_PER_SLOT = {"plain": 1, "gemm_sort": 4, "gemm_prep": 3, "gemm_screen": 1,
+                    "gemm_exact": 1, "gemm_finalize": 2}
 
 
 def time_mode(binding, at, fib, labels, dst, mode, steps, warmup, stream, world, dist, dev):
@@ -239,8 +248,8 @@ def time_mode(binding, at, fib, labels, dst, mode, steps, warmup, stream, world,
     for k in LAUNCH_SLOTS:
         c, t = binding.seg_profile_read(at, k)
         if c:
-            kern[k] = {"launches": c, "ms_per_launch": t / c}
-            launches += c
+            kern[k] = {"launches": c * KERNELS_PER_SLOT[k], "ms_per_step": t / c}
+            launches += c * KERNELS_PER_SLOT[k]
     binding.seg_profile_enable(at, False)
     t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if world > 1:
@@ -360,49 +369,67 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    # FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FMA) x max SM clock
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    alu_src = (f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max clock; {pk_src} "
+               f"clock)")
+    bf16 = float(pk.get("bf16_tflops", 1900.0))
     roofs = {}
     for mode, r in results.items():
-        kname = DOMINANT[mode]
-        k = r["kernels"].get(kname)
-        if not k:
-            continue
-        sec = k["ms_per_launch"] / 1000.0
-        if mode == "plain":
-            # FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FMA) x max SM clock
-            peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
-            alg = n * atlas_np.M * pdpp * 8.0
-            roofs[mode] = {"bound": "alu", "kernel": KERNEL_NAME[kname],
-                           "achieved": alg / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
-                           "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                          f"(max clock; {pk_src} clock)",
-                           "algorithmic": f"{pdpp:.4f} point distances per pair (oracle "
-                                          f"cascade counts) x 8 flop x {n} x {atlas_np.M} "
-                                          f"pairs"}
-        else:
-            bf16 = float(pk.get("bf16_tflops", 1900.0))
-            peak = bf16 if mode.endswith("bf16") else bf16 * (1.1 / 2.25)
-            cols = atlas_np.M if "inv" in mode else 2 * atlas_np.M
-            alg = 2.0 * n * 64 * cols
-            roofs[mode] = {"bound": "tensor", "kernel": KERNEL_NAME[kname],
-                           "achieved": alg / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
-                           "peak_source": ("measured bf16 burst" if mode.endswith("bf16") else
-                                           "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)")
-                                          + f" ({pk_src})",
-                           "algorithmic": f"2 x {n} fibers x K=64 x {cols} columns"}
-        roofs[mode]["frac"] = roofs[mode]["achieved"] / roofs[mode]["peak"]
-        roofs[mode]["traffic"] = traffic_for(KERNEL_NAME[kname])
-        roofs[mode]["ms_per_launch"] = k["ms_per_launch"]
+        mr = {}
+        for kname, k in r["kernels"].items():
+            sec = k["ms_per_step"] / 1000.0
+            if kname == "plain":
+                alg = n * atlas_np.M * pdpp * 8.0
+                mr[kname] = {"bound": "alu", "achieved": alg / sec / 1e12, "peak": alu_peak,
+                             "unit": "TFLOP/s", "peak_source": alu_src,
+                             "algorithmic": f"{pdpp:.4f} point distances per pair (oracle "
+                                            f"cascade counts) x 8 flop x {n} x {atlas_np.M} "
+                                            f"pairs"}
+            elif kname == "gemm_screen":
+                st = r["gemm_stats"]
+                kdim = 32 if "inv" in mode else 64
+                alg = 2.0 * st["screened"] * kdim
+                peak = bf16 if mode.endswith("bf16") else bf16 * (1.1 / 2.25)
+                mr[kname] = {"bound": "tensor", "achieved": alg / sec / 1e12, "peak": peak,
+                             "unit": "TFLOP/s",
+                             "peak_source": ("measured bf16 burst" if mode.endswith("bf16") else
+                                             "measured bf16 burst x 1.1/2.25 (nominal "
+                                             "TF32/BF16)") + f" ({pk_src})",
+                             "algorithmic": f"2 x K={kdim} x {st['screened']} pairs in the "
+                                            f"computed blocks (of {st['pairs']}; the rest "
+                                            f"culled on centre-point boxes)"}
+            elif kname == "gemm_exact":
+                st = r["gemm_stats"]
+                alg = 8.0 * st["point_distances"]
+                mr[kname] = {"bound": "alu", "achieved": alg / sec / 1e12, "peak": alu_peak,
+                             "unit": "TFLOP/s", "peak_source": alu_src,
+                             "algorithmic": f"{st['point_distances']} squared point distances "
+                                            f"(counted by the kernel) x 8 flop, "
+                                            f"{st['survivors']} survivor pairs"}
+            else:
+                continue
+            mr[kname]["kernel"] = KERNEL_NAME[kname]
+            mr[kname]["frac"] = mr[kname]["achieved"] / mr[kname]["peak"]
+            mr[kname]["traffic"] = traffic_for(KERNEL_NAME[kname])
+            mr[kname]["ms_per_launch"] = k["ms_per_step"]
+            mr[kname]["share_of_step"] = k["ms_per_step"] / r["ms_per_step"]
+        roofs[mode] = mr
+    # the headline's roofline is that of its dominant kernel (the largest share of the step)
+    dom = max(hr["kernels"], key=lambda k: hr["kernels"][k]["ms_per_step"])
+    head_roof = roofs[head].get(dom)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if head == "plain" else ("bf16" if head.endswith("bf16") else "tf32"),
+            "dtype": "f32" if head == "plain" else
+                     ("bf16+f32" if head.endswith("bf16") else "tf32+f32"),
             "data": "synthetic",
             "config": {"workload": args.workload, "fibers": n, "centroids": atlas_np.M,
                        "bundles": atlas_np.B, "points": 21, "mode": head,
                        "tile_config": hr["config"],
                        "l2": "inputs larger than L2 (1.04 GB of fibers)",
                        "parallelism": f"dp{world} (one subject per rank)"},
-            "roofline": roofs.get(head), "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": head_roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(round(hr["launches_per_step"] * args.steps)),
             "clocks": clk,
             "modes": {m: {k: v for k, v in r.items()} for m, r in results.items()},

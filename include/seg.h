@@ -189,8 +189,8 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
  * library launches for it records a pair of CUDA events on its stream (no host synchronisation).
  * seg_profile_read waits for those events and returns, for one kernel name, the number of
  * launches and their summed duration in milliseconds since profiling was (re)enabled.
- * Kernel names: "plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
- * "gemm_finalize", "grad", "gemm_sort". Enabling (or disabling) clears what was recorded.
+ * Kernel names: "plain", "batch", "gemm_sort", "gemm_prep" (their launches precede the
+ * screen), "gemm_screen", "gemm_exact", "gemm_finalize", "grad". Enabling (or disabling) clears what was recorded.
  */
 seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable);
 seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launches,
@@ -208,10 +208,13 @@ seg_status seg_sync_status(const seg_atlas* atlas, void* stream);
  * candidates inside the (128-fiber x N-column) blocks the tensor cores computed (blocks whose
  * centre-point boxes lie farther apart than every threshold are skipped; padding included),
  * survivors = candidates kept by the tensor-core bound, overflow_fibers = fibers rescanned by
- * the exact kernel because the survivor list was full. Any pointer may be NULL.
+ * the exact kernel because the survivor list was full, point_distances = squared point
+ * distances the exact re-check of the survivors evaluated (the rescan not included). Any
+ * pointer may be NULL.
  */
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
-                          int64_t* overflow_fibers, int64_t* screened);
+                          int64_t* overflow_fibers, int64_t* screened,
+                          int64_t* point_distances);
 
 #ifdef __cplusplus
 }

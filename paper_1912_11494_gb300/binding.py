@@ -40,7 +40,7 @@ SIGNATURES = [
     ("seg_set_config", ctypes.c_int, [_P, ctypes.c_int, _I32]),
     ("seg_get_config", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I32)]),
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
-                                      ctypes.POINTER(_I64),
+                                      ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
     ("seg_profile_enable", ctypes.c_int, [_P, _I32]),
     ("seg_profile_read", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64),
@@ -232,14 +232,15 @@ def seg_sync_status(atlas: Atlas, stream=None):
 
 
 def seg_gemm_stats(atlas: Atlas):
-    p, s, o, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    p, s, o, c, d = (ctypes.c_int64() for _ in range(5))
     _check(lib().seg_gemm_stats(atlas.handle, ctypes.byref(p), ctypes.byref(s), ctypes.byref(o),
-                                ctypes.byref(c)))
-    return dict(pairs=p.value, survivors=s.value, overflow_fibers=o.value, screened=c.value)
+                                ctypes.byref(c), ctypes.byref(d)))
+    return dict(pairs=p.value, survivors=s.value, overflow_fibers=o.value, screened=c.value,
+                point_distances=d.value)
 
 
-PROFILED_KERNELS = ("plain", "batch", "gemm_prep", "gemm_screen", "gemm_exact", "gemm_rescan",
-                    "gemm_finalize", "grad", "gemm_sort")
+PROFILED_KERNELS = ("plain", "batch", "gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact",
+                    "gemm_finalize", "grad")
 
 
 def seg_profile_enable(atlas: Atlas, enable: bool = True):

@@ -27,9 +27,9 @@
 // warp compare the individual values and write a block record (32 fibers x 32 columns, one
 // column mask per fiber). A second kernel runs the exact test of Section 2.3 on every survivor
 // of every block and merges the result into the fiber's packed key with atomicMin (same key as
-// the plain kernel, so the tie rule of Algorithm 1 holds); fibers whose survivors did not fit
-// the record list are rescanned by an exact kernel; a last kernel writes labels and distances
-// in the caller's order.
+// the plain kernel, so the tie rule of Algorithm 1 holds); the fibers whose survivors did not
+// fit the record list are rescanned exactly, and a last kernel writes labels and distances in
+// the caller's order.
 //
 // Orientation-free variant (SEG_MODE_GEMM_INV_*). With c = a_10 and s_i = (a_i + a_(20-i))/2,
 // for x_i = a_i - b_i, y_i = a_(20-i) - b_(20-i) (or the reversed pairing) the identity
@@ -95,7 +95,8 @@ struct GemmScratch {
     uint2* hdr;                   // [cap] {first sorted fiber, first column} or EMPTY_SLOT
     unsigned* mask;               // [cap][32] surviving columns of each of the 32 fibers
     unsigned long long* cnt;      // [0] records reserved, [1] fibers flagged, [2] survivors,
-                                  // [3] pairs in the blocks the tensor cores computed
+                                  // [3] pairs in the blocks the tensor cores computed, [4] run
+                                  // counter of the exact kernel, [5] its point distances
     long long cap;
 };
 
@@ -927,7 +928,8 @@ constexpr unsigned DONE_ENTRY = 0xFFFFFFFFu;  // queue entry already tested
 template <bool INV>
 __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float* s_fib,
                                             const float* s_cen, const int* s_sidx,
-                                            unsigned* s_best, unsigned long long* key) {
+                                            unsigned* s_best, unsigned long long* key,
+                                            unsigned& npd) {
     const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
     const int j = INV ? bit : bit >> 1;
     const float* a = s_fib + lo * FS_STRIDE;
@@ -939,17 +941,17 @@ __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float
     if (INV) {
         bool ad = ((ent >> 10) & 1u) && md <= bound;
         bool ar = ((ent >> 11) & 1u) && mr <= bound;
-        if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; }
-        if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; }
-        if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; }
-        if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; }
+        if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; npd += 4; }
+        if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; npd += 4; }
+        if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; npd += 14; }
+        if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; npd += 14; }
         pass = ad || ar;
         if (ad && (!ar || md <= mr)) { d2 = md; o = 0; } else { d2 = mr; o = 1; }
     } else {
         o = bit & 1;
         pass = md <= bound;
-        if (pass) { md = o ? mid4<1>(a, b, md) : mid4<0>(a, b, md); pass = md <= bound; }
-        if (pass) { md = o ? rest17<1>(a, b, md) : rest17<0>(a, b, md); pass = md <= bound; }
+        if (pass) { md = o ? mid4<1>(a, b, md) : mid4<0>(a, b, md); pass = md <= bound; npd += 4; }
+        if (pass) { md = o ? rest17<1>(a, b, md) : rest17<0>(a, b, md); pass = md <= bound; npd += 14; }
         d2 = md;
     }
     if (pass) {
@@ -979,6 +981,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
     // fiber rows (kept in shared memory) and each fiber's best so far.
     long long blk = 0, blk_end = 0;
     unsigned cur = EMPTY_SLOT;  // first fiber of the rows in s_fib
+    unsigned npd = 0;           // point distances this thread evaluated (statistics)
     uint2 hn = make_uint2(EMPTY_SLOT, 0u);  // the next record's header and masks, loaded one
     unsigned mn = 0u;                       // record ahead
     for (;;) {
@@ -1053,15 +1056,18 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 const float* b = s_cen + (INV ? bit : bit >> 1) * EX_STRIDE;
                 const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
                 const float c = pd2(a, CENTRE, b, CENTRE);
+                npd += 1;
                 if (c <= bound) {
                     bool ad, ar = false;
                     if (INV) {
                         md = fmaxf(c, ends2<0>(a, b));
+                        npd += 4;
                         mr = fmaxf(c, ends2<1>(a, b));
                         ad = md <= bound;
                         ar = mr <= bound;
                     } else {
                         md = fmaxf(c, (bit & 1) ? ends2<1>(a, b) : ends2<0>(a, b));
+                        npd += 2;
                         ad = md <= bound;
                     }
                     push = ad || ar;
@@ -1089,7 +1095,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         // bound; phase B2: the rest of the queue
         if (tid < 32 && s_first[tid] != ~0ull) {
             const unsigned q = (unsigned)s_first[tid];
-            exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x);
+            exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x, npd);
             s_q[q] = DONE_ENTRY;
         }
         __syncthreads();
@@ -1097,15 +1103,20 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         for (unsigned q = tid; q < nq; q += EX_THREADS) {
             const unsigned ent = s_q[q];
             if (ent != DONE_ENTRY)
-                exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x);
+                exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x, npd);
         }
         __syncthreads();  // the buffers are refilled for the next record
     }
+    unsigned long long tot = npd;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, off);
+    if (lane == 0 && tot) atomicAdd(g.cnt + 5, tot);
 }
 
-// Fibers whose survivors did not fit the list: exact scan against the whole atlas.
-__global__ void k_overflow_rescan(const float* __restrict__ fib, long long n, AtlasView at,
-                                  GemmScratch g) {
+// Fibers whose survivors did not fit the record list: exact scan against the whole atlas (the
+// kernel returns at once when no fiber was flagged).
+__global__ void k_overflow_rescan(long long n, AtlasView at, GemmScratch g) {
+    if (*(volatile unsigned long long*)(g.cnt + 1) == 0) return;
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n || g.flag[f] == 0) return;
     const float* src = g.fs + (size_t)f * CROW;
@@ -1121,6 +1132,7 @@ __global__ void k_overflow_rescan(const float* __restrict__ fib, long long n, At
     }
 }
 
+// Labels and distances in the caller's order.
 __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __restrict__ labels,
                            float* __restrict__ dist, int* __restrict__ cidx,
                            unsigned char* __restrict__ orient, long long pairs,
@@ -1131,6 +1143,7 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __rest
         stats[1] = (long long)g.cnt[2];
         stats[2] = (long long)g.cnt[1];
         stats[3] = (long long)g.cnt[3];
+        stats[4] = (long long)g.cnt[5];
     }
     if (f >= n) return;
     const unsigned long long k = g.key[f];
@@ -1239,8 +1252,8 @@ int gemm_num_configs() { return kNumShapes; }
 seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g,
                            cudaStream_t st) {
     cudaError_t e;
-    if ((e = cudaMalloc(&g->stats, 4 * sizeof(long long))) ||
-        (e = cudaMemsetAsync(g->stats, 0, 4 * sizeof(long long), st)))
+    if ((e = cudaMalloc(&g->stats, 5 * sizeof(long long))) ||
+        (e = cudaMemsetAsync(g->stats, 0, 5 * sizeof(long long), st)))
         return cuda_fail(e, "gemm stats");
     if ((e = cudaMalloc(&g->sp_s, (size_t)at.M * sizeof(int))) ||
         (e = cudaMalloc(&g->cen_sp, (size_t)at.M * CROW * sizeof(float))) ||
@@ -1415,12 +1428,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         e = cudaGetLastError();
     }
     if (!e) {
-        ProfScope ps(prof, PROF_GEMM_RESCAN, st);
-        k_overflow_rescan<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fib, n, at, g);
-        e = cudaGetLastError();
-    }
-    if (!e) {
         ProfScope ps(prof, PROF_GEMM_FINAL, st);
+        k_overflow_rescan<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, at, g);
         k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
             n, at, g, labels, dist, cidx, orient, n * (long long)cols, ga->stats);
         e = cudaGetLastError();

@@ -434,8 +434,7 @@ seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launc
     g_last_error.clear();
     if (!atlas || !kernel) return fail(SEG_ERR_INVALID_ARG, "seg_profile_read: NULL argument");
     static const char* names[PROF_SLOTS] = {"plain", "batch", "gemm_prep", "gemm_screen",
-                                            "gemm_exact", "gemm_rescan", "gemm_finalize", "grad",
-                                            "gemm_sort"};
+                                            "gemm_exact", "gemm_finalize", "grad", "gemm_sort"};
     int slot = -1;
     for (int k = 0; k < PROF_SLOTS; ++k)
         if (strcmp(kernel, names[k]) == 0) slot = k;
@@ -473,10 +472,11 @@ seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
 }
 
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
-                          int64_t* overflow_fibers, int64_t* screened) {
+                          int64_t* overflow_fibers, int64_t* screened,
+                          int64_t* point_distances) {
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_stats: atlas is NULL");
-    long long h[4] = {0, 0, 0, 0};
+    long long h[5] = {0, 0, 0, 0, 0};
     if (atlas->gemm.stats) {
         cudaError_t e = cudaMemcpy(h, atlas->gemm.stats, sizeof(h), cudaMemcpyDeviceToHost);
         if (e) return cuda_fail(e, "seg_gemm_stats");
@@ -485,6 +485,7 @@ seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survi
     if (survivors) *survivors = h[1];
     if (overflow_fibers) *overflow_fibers = h[2];
     if (screened) *screened = h[3];
+    if (point_distances) *point_distances = h[4];
     return SEG_OK;
 }
 

@@ -65,4 +65,4 @@ def test_argument_errors_before_device_work(lib):
     assert lib.seg_destroy_atlas(None) == 0
     assert lib.seg_apply_affine(None, -1, None, None, None) == 1
     assert lib.seg_apply_affine(None, 0, None, None, None) == 1
-    assert lib.seg_gemm_stats(None, None, None, None, None) == 1
+    assert lib.seg_gemm_stats(None, None, None, None, None, None) == 1
