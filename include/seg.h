@@ -116,6 +116,20 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
                      void* stream);
 
 /*
+ * seg_label on host buffers (not in the paper): h_fibers host float32 [n][21][3], h_labels host
+ * int32 [n] (required), h_dist host float32 [n] or NULL. The subject is split into up to
+ * SEG_HOST_CHUNKS chunks; chunk c+1 is uploaded on an internal stream while chunk c is labelled
+ * (seg_label on `stream`, so the results equal seg_label's), and each chunk's results are
+ * copied back on `stream`. Asynchronous: the host buffers must stay valid and unread until
+ * `stream` completes. Page-locked (cudaHostAlloc) buffers let the copies overlap the labelling;
+ * pageable ones work but serialise. The atlas owns the device copies (grown on demand; calls on
+ * one atlas are serialised on the host).
+ */
+#define SEG_HOST_CHUNKS 4
+seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t n,
+                          seg_mode mode, int32_t* h_labels, float* h_dist, void* stream);
+
+/*
  * Label nsubj subjects of uneven size in one persistent launch (not in the paper; the paper
  * labels one subject at a time, Section 3). Subject s has h_counts[s] >= 0 fibers at device
  * pointer h_fibers[s] and writes h_labels[s] (required) and h_dist[s] (array or entries may be

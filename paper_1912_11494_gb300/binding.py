@@ -31,6 +31,7 @@ SIGNATURES = [
     ("seg_destroy_atlas", ctypes.c_int, [_P]),
     ("seg_atlas_info", ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     ("seg_label", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _P, _P, _P, _P]),
+    ("seg_label_host", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _P, _P]),
     ("seg_label_batch", ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_int, _P, _P, _P]),
     ("seg_apply_affine", ctypes.c_int, [_P, _I64, _P, _P, _P]),
     ("seg_grad", ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
@@ -155,6 +156,17 @@ def label(atlas: Atlas, fibers, mode="plain", stream=None, want_cidx=True):
     orient = torch.empty(n, dtype=torch.uint8, device=dev) if want_cidx else None
     seg_label(atlas, fib, mode, labels, dist, cidx, orient, stream)
     return labels, dist, cidx, orient
+
+
+def seg_label_host(atlas: Atlas, fibers, mode, labels, dist=None, stream=None):
+    """Enqueue labelling of host (CPU, ideally pinned) tensors: fibers [n,21,3] float32 into
+    labels [n] int32 and dist [n] float32 (or None); read them after the stream completes."""
+    for name, t in (("fibers", fibers), ("labels", labels), ("dist", dist)):
+        if t is not None and (t.device.type != "cpu" or not t.is_contiguous()):
+            raise SegError(1, f"seg_label_host: {name} must be a contiguous CPU tensor")
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(lib().seg_label_host(atlas.handle, _ptr(fibers), int(fibers.shape[0]), m,
+                                _ptr(labels), _ptr(dist), _stream(stream)))
 
 
 def seg_label_batch(atlas: Atlas, fibers_list, mode, labels_list, dist_list=None, stream=None):

@@ -124,6 +124,13 @@ struct seg_atlas {
     unsigned* status = nullptr;
     GemmAtlas gemm{};
     ScratchArena scratch{};
+    // seg_label_host: device copies of the caller's host buffers, an internal copy stream and
+    // one event per chunk (guarded by host_mu: calls on one atlas share the buffers)
+    void* hbuf = nullptr;
+    size_t hbuf_bytes = 0;
+    cudaStream_t hcopy = nullptr;
+    cudaEvent_t hev[SEG_HOST_CHUNKS + 2] = {};
+    std::mutex host_mu;
     BatchState batch{};
     int config[5] = {0, 0, 0, 0, 0};  // tile-shape selection per seg_mode
     Profiler prof;
@@ -159,6 +166,11 @@ static void free_atlas(seg_atlas* a) {
     cudaFree(a->status);
     free_gemm_atlas(&a->gemm);
     free_scratch(&a->scratch);
+    if (a->hcopy) cudaStreamSynchronize(a->hcopy);
+    for (cudaEvent_t ev : a->hev)
+        if (ev) cudaEventDestroy(ev);
+    if (a->hcopy) cudaStreamDestroy(a->hcopy);
+    cudaFree(a->hbuf);
     free_batch(&a->batch);
     delete a;
 }
@@ -317,6 +329,69 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
     }
     return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n, (int)mode, d_labels,
                       d_dist, d_cidx, d_orient, st, a->config[(int)mode], &a->prof);
+}
+
+seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t n,
+                          seg_mode mode, int32_t* h_labels, float* h_dist, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_host: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_host: n=%lld < 0", (long long)n);
+    if (n > 0 && (!h_fibers || !h_labels))
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_host: NULL fibers or labels");
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_GEMM_INV_TF32)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_host: unknown mode %d", (int)mode);
+    if (n == 0) return SEG_OK;
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(a->host_mu);
+    cudaError_t e;
+    if (!a->hcopy) {
+        if ((e = cudaStreamCreateWithFlags(&a->hcopy, cudaStreamNonBlocking)))
+            return cuda_fail(e, "seg_label_host: stream");
+        for (cudaEvent_t& ev : a->hev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)))
+                return cuda_fail(e, "seg_label_host: event");
+    }
+    cudaEvent_t ev_start = a->hev[SEG_HOST_CHUNKS], ev_done = a->hev[SEG_HOST_CHUNKS + 1];
+    const size_t fb = ((size_t)n * NC * 4 + 255) / 256 * 256, lb = ((size_t)n * 4 + 255) / 256 * 256;
+    const size_t need = fb + 2 * lb;
+    if (need > a->hbuf_bytes) {
+        // the previous call's copies and kernels may still use the old buffer
+        if ((e = cudaEventSynchronize(ev_done)) || (e = cudaFree(a->hbuf)))
+            return cuda_fail(e, "seg_label_host: buffer");
+        a->hbuf = nullptr;
+        a->hbuf_bytes = 0;
+        if ((e = cudaMalloc(&a->hbuf, need))) return cuda_fail(e, "seg_label_host: buffer");
+        a->hbuf_bytes = need;
+    }
+    float* d_fib = static_cast<float*>(a->hbuf);
+    int32_t* d_lab = reinterpret_cast<int32_t*>(static_cast<char*>(a->hbuf) + fb);
+    float* d_dst = reinterpret_cast<float*>(static_cast<char*>(a->hbuf) + fb + lb);
+    // the copies start after everything already queued on the caller's stream (which includes
+    // the previous call's use of the buffer)
+    if ((e = cudaEventRecord(ev_start, st)) || (e = cudaStreamWaitEvent(a->hcopy, ev_start, 0)))
+        return cuda_fail(e, "seg_label_host: ordering");
+    const int chunks = n >= (1 << 21) ? SEG_HOST_CHUNKS : n >= (1 << 19) ? 2 : 1;
+    const int64_t per = (n + chunks - 1) / chunks;
+    for (int c = 0; c < chunks; ++c) {
+        const int64_t off = c * per, len = std::min<int64_t>(per, n - off);
+        if (len <= 0) break;
+        if ((e = cudaMemcpyAsync(d_fib + off * NC, h_fibers + off * NC, (size_t)len * NC * 4,
+                                 cudaMemcpyHostToDevice, a->hcopy)) ||
+            (e = cudaEventRecord(a->hev[c], a->hcopy)) ||
+            (e = cudaStreamWaitEvent(st, a->hev[c], 0)))
+            return cuda_fail(e, "seg_label_host: upload");
+        seg_status s = seg_label(atlas, d_fib + off * NC, len, mode, d_lab + off,
+                                 h_dist ? d_dst + off : nullptr, nullptr, nullptr, stream);
+        if (s != SEG_OK) return s;
+        if ((e = cudaMemcpyAsync(h_labels + off, d_lab + off, (size_t)len * 4,
+                                 cudaMemcpyDeviceToHost, st)) ||
+            (h_dist && (e = cudaMemcpyAsync(h_dist + off, d_dst + off, (size_t)len * 4,
+                                            cudaMemcpyDeviceToHost, st))))
+            return cuda_fail(e, "seg_label_host: download");
+    }
+    if ((e = cudaEventRecord(ev_done, st))) return cuda_fail(e, "seg_label_host: event");
+    return SEG_OK;
 }
 
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,

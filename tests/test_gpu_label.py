@@ -180,6 +180,28 @@ def test_gemm_locality_order_extremes(dev, mode):
     parity.compare(fib, a.centroids, a.bundle_of, a.thresholds, *got)
 
 
+@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "gemm_inv_tf32"])
+def test_host_buffers_equal_device_call(dev, mode, full_size):
+    """seg_label_host (chunked upload overlapping the labelling) returns seg_label's results,
+    for 4 chunks (the full subject, pinned buffers), 2 chunks and 1 chunk (pageable buffers),
+    and again on the same atlas after a smaller call (buffer reuse)."""
+    atlas_np, fib = full_size
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    for n, pinned in ((len(fib), True), (700_000, False), (100_003, False), (len(fib), False)):
+        f = fib[:n]
+        ref_lab, ref_dist, _, _ = run(at, f, dev, mode)
+        h_fib = torch.as_tensor(np.ascontiguousarray(f))
+        h_lab = torch.full((n,), -7, dtype=torch.int32)
+        h_dst = torch.full((n,), -7.0)
+        if pinned:
+            h_fib, h_lab, h_dst = h_fib.pin_memory(), h_lab.pin_memory(), h_dst.pin_memory()
+        binding.seg_label_host(at, h_fib, mode, h_lab, h_dst)
+        torch.cuda.synchronize()
+        binding.seg_sync_status(at)
+        np.testing.assert_array_equal(h_lab.numpy(), ref_lab)
+        np.testing.assert_array_equal(h_dst.numpy(), ref_dist)
+
+
 def test_every_tile_shape_identical(dev, small_workload):
     """All tile-shape configurations of a mode compute the same labels, distances, centroids."""
     atlas_np, fib = small_workload
