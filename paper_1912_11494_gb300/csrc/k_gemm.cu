@@ -86,8 +86,9 @@ struct GemmScratch {
     float* alpha;                 // [n_pad] (sorted order, as key and flag)
     unsigned long long* key;      // [n]
     unsigned char* flag;          // [n] survivors dropped for lack of list space
-    const unsigned long long* amask;  // [n_units][awords] bit t: the unit's block with tile t
-                                      // is computed (the others are culled)
+    const unsigned long long* amask;  // [n_units][awords] bit c: the unit's 32-column chunk c
+                                      // may hold survivors (a tile is computed when any of its
+                                      // chunks may; the epilogue reads only those chunks)
     int awords;
     const float* cen_sp;          // the atlas's spatial-order arrays (GemmAtlas)
     const float* thr2_sp;
@@ -453,7 +454,16 @@ __device__ inline bool block_active(const UnitBox& b, const float4* __restrict__
     return !(lb2 > lo.w * 1.0001f + 1e-3f);  // lo.w: max theta^2 of the tile
 }
 
-constexpr int MAXW = 8;  // mask words per unit: at most 512 column tiles
+constexpr int MAXW = 16;  // mask words per unit: at most 1024 chunks (32768 columns)
+
+// The next tile with an active chunk in `bits` (word wd of a unit's chunk mask, CPT chunks per
+// tile); clears that tile's bits.
+template <int CPT>
+__device__ __forceinline__ int next_tile(unsigned long long& bits, int wd) {
+    const int gi = (__ffsll((long long)bits) - 1) / CPT;
+    bits &= ~(((1ull << CPT) - 1) << (gi * CPT));
+    return wd * (64 / CPT) + gi;
+}
 
 struct UnitMask {
     unsigned long long w[MAXW];
@@ -470,23 +480,26 @@ struct UnitMask {
     }
 };
 
-// Active-block masks: one thread per work unit of R x 128 sorted fibers, one bit per tile.
+// Active-chunk masks: one thread per work unit of R x 128 sorted fibers, one bit per 32-column
+// chunk.
 __global__ void k_block_mask(const float4* __restrict__ ubox, const float4* __restrict__ tbox,
-                             long long n_units, int R, int n_tiles, int words,
+                             long long n_units, int R, int n_chunks, int words,
                              unsigned long long* __restrict__ amask) {
-    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per unit; lane l tests chunks 32k + l
+    const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (u >= n_units) return;
     const UnitBox b = unit_box(ubox, u, R);
     for (int wd = 0; wd < words; ++wd) {
-        unsigned long long m = 0;
-        for (int k = 0; k < 64 && wd * 64 + k < n_tiles; ++k)
-            if (block_active(b, tbox, wd * 64 + k)) m |= 1ull << k;
-        amask[u * words + wd] = m;
+        const int c0 = wd * 64 + lane, c1 = c0 + 32;
+        const unsigned lo = __ballot_sync(0xffffffffu, c0 < n_chunks && block_active(b, tbox, c0));
+        const unsigned hi = __ballot_sync(0xffffffffu, c1 < n_chunks && block_active(b, tbox, c1));
+        if (lane == 0) amask[u * words + wd] = ((unsigned long long)hi << 32) | lo;
     }
 }
 
-// Centre-point box and max theta^2 of each tile of `per` consecutive spatial centroids (an
-// empty tile never passes).
+// Centre-point box and max theta^2 of each 32-column chunk (`per` consecutive spatial
+// centroids; an empty chunk never passes).
 __global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, int n_tiles,
                            float4* __restrict__ tbox) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -598,6 +611,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               long long n_units, int n_tiles, int cols, GemmScratch g, unsigned* status) {
     using C = GemmCfg<FMT, KE, R, N, S, ABUF>;
+    constexpr int CPT = N / 32;  // 32-column chunks per tile
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
@@ -672,8 +686,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 (int)((u * R + r) * 128), a_full + ab);
 #pragma unroll 1
             for (int wd = 0; wd < MAXW && ok; ++wd)
-            for (unsigned long long bits = um.w[wd]; bits; bits &= bits - 1) {
-                const int t = wd * 64 + __ffsll((long long)bits) - 1;
+            for (unsigned long long bits = um.w[wd]; bits;) {
+                const int t = next_tile<CPT>(bits, wd);
                 if (!W.wait(b_empty + stage, ((b_phase >> stage) & 1u) ^ 1u)) {
                     ok = false;
                     break;
@@ -718,10 +732,12 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const long long use = ABUF == 2 ? (it >> 1) : it;
             if (!W.wait(a_full + ab, (uint32_t)(use & 1))) break;
             tc_fence_after();
-            const uint32_t sA = smem_u32(smem + C::A_OFF + ab * R * C::A_TILE);
+            const uint64_t ad_unit =
+                make_sdesc<C::REGB>(smem_u32(smem + C::A_OFF + ab * R * C::A_TILE));
 #pragma unroll 1
             for (int wd = 0; wd < MAXW && ok; ++wd)
-            for (unsigned long long bits = um.w[wd]; bits; bits &= bits - 1) {
+            for (unsigned long long bits = um.w[wd]; bits;) {
+                (void)next_tile<CPT>(bits, wd);
                 ++active;
                 const int cb = (int)(tile % C::NACC);
                 const long long cuse = tile / C::NACC;
@@ -735,17 +751,19 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sB = smem_u32(smem + C::B_OFF + stage * C::B_TILE);
+                // descriptors of the stage's first K step; step kk starts 32 kk bytes into the
+                // row (region, then offset), added to the address field (16-byte units)
+                const uint64_t bd0 = make_sdesc<C::REGB>(
+                    smem_u32(smem + C::B_OFF + stage * C::B_TILE));
                 for (int r = 0; r < R; ++r) {
                     const uint32_t d = tmem + (uint32_t)(cb * C::ACC_COLS + r * N);
+                    const uint64_t ad0 = ad_unit + (uint64_t)((r * C::A_TILE) >> 4);
 #pragma unroll
                     for (int kk = 0; kk < C::KSTEPS; ++kk) {
-                        // K step kk starts 32 kk bytes into the row: region, then offset
                         const int reg = (kk * 32) / C::REGB;
                         const uint32_t koff = (uint32_t)((kk * 32) % C::REGB);
-                        const uint64_t ad = make_sdesc<C::REGB>(sA + r * C::A_TILE +
-                                                                reg * C::A_REGION + koff);
-                        const uint64_t bd = make_sdesc<C::REGB>(sB + reg * C::B_REGION + koff);
+                        const uint64_t ad = ad0 + (uint64_t)((reg * C::A_REGION + koff) >> 4);
+                        const uint64_t bd = bd0 + (uint64_t)((reg * C::B_REGION + koff) >> 4);
                         if (FMT == 1)
                             mma_f16(d, ad, bd, idesc, kk > 0);
                         else
@@ -784,10 +802,16 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             for (int r = 0; r < 4; ++r)
                 al[r] = r < R ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane) : INFINITY;
             const unsigned fib0 = (unsigned)(u * R * 128 + 32 * q + lane);
+            // the unit's mask words, one per lane, handed out by shuffles
+            const unsigned long long mword =
+                lane < g.awords ? __ldg(g.amask + u * g.awords + lane) : 0ull;
             for (int wd = 0; wd < g.awords && ok; ++wd)
-            for (unsigned long long bits = __ldg(g.amask + u * g.awords + wd); bits;
-                 bits &= bits - 1) {
-                const int t = wd * 64 + __ffsll((long long)bits) - 1;
+            for (unsigned long long bits = __shfl_sync(0xffffffffu, mword, wd); bits;) {
+                const unsigned long long word = bits;
+                const int t = next_tile<CPT>(bits, wd);
+                // this tile's chunk bits: chunk c of the tile's columns may hold survivors
+                const unsigned tb =
+                    (unsigned)((word >> ((t % (64 / CPT)) * CPT)) & ((1ull << CPT) - 1));
                 const int cb = (int)(tile % C::NACC);
                 if (!W.wait(acc_full + cb, (uint32_t)((tile / C::NACC) & 1))) {
                     ok = false;
@@ -798,13 +822,17 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll 1
                 for (int c0 = sub; c0 < CHUNKS; c0 += 2 * EPI_SUB) {
                     float v[2][32], mx[2];
-                    tmem_ld_red32(tbase + (uint32_t)(32 * c0), v[0], mx[0]);
-                    const bool two = c0 + EPI_SUB < CHUNKS;
-                    if (two) tmem_ld_red32(tbase + (uint32_t)(32 * (c0 + EPI_SUB)), v[1], mx[1]);
+                    // chunks whose centroid box is out of reach are not read
+                    const bool act0 = (tb >> (c0 % CPR)) & 1u;
+                    const bool act1 = c0 + EPI_SUB < CHUNKS && ((tb >> ((c0 + EPI_SUB) % CPR)) & 1u);
+                    if (!act0 && !act1) continue;
+                    if (act0) tmem_ld_red32(tbase + (uint32_t)(32 * c0), v[0], mx[0]);
+                    if (act1) tmem_ld_red32(tbase + (uint32_t)(32 * (c0 + EPI_SUB)), v[1], mx[1]);
                     tmem_wait_ld();
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        if (h == 1 && !two) break;
+                        if (h == 0 && !act0) continue;
+                        if (h == 1 && !act1) break;
                         const int c = c0 + EPI_SUB * h;
                         const int r = c / CPR;
                         const float a = r == 0 ? al[0] : r == 1 ? al[1] : r == 2 ? al[2] : al[3];
@@ -1319,11 +1347,12 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const int n_tiles = cols_pad / sh.N;
     if (n_pad >= (1LL << 32))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
-    const int awords = (n_tiles + 63) / 64;
+    const int n_chunks = cols_pad / 32;
+    const int awords = (n_chunks + 63) / 64;
     if (awords > MAXW)
         return fail(SEG_ERR_UNSUPPORTED,
-                    "seg_label: %d column tiles of %d exceed the GEMM modes' limit of %d", n_tiles,
-                    sh.N, 64 * MAXW);
+                    "seg_label: %d operand columns exceed the GEMM modes' limit of %d", cols_pad,
+                    32 * 64 * MAXW);
     // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for 16
     // per 32 fibers + slack (fibers past the room are rescanned exactly)
     const long long cap = n_pad / 32 * 16 + 65536;
@@ -1339,7 +1368,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const size_t off_fs = off_top + (size_t)NTOP * 4;
     const size_t off_ubox = off_fs + (size_t)n_pad * CROW * 4;
     const size_t off_tbox = off_ubox + align256((size_t)(n_pad / 32) * 32);
-    const size_t off_amask = off_tbox + align256((size_t)n_tiles * 32);
+    const size_t off_amask = off_tbox + align256((size_t)n_chunks * 32);
     const size_t off_hdr = off_amask + align256((size_t)n_units * awords * 8);
     const size_t off_mask = off_hdr + align256((size_t)cap * 8);
     const size_t bytes = off_mask + (size_t)cap * 128;
@@ -1403,15 +1432,14 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
                          : (inv ? k_prep_a<1, true> : k_prep_a<1, false>);
         prep<<<pb, PREP_WARPS * 32, 0, st>>>(fib, perm, n, n_pad, at, g.a, g.alpha, g.key, g.fs,
                                              ubox);
-        // centroids per column tile: N (orientation-free) or N / 2 (directional)
+        // centroids per 32-column chunk: 32 (orientation-free) or 16 (directional)
         if (!e) e = cudaGetLastError();
         if (!e)
-            k_tile_box<<<(n_tiles + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M,
-                                                             inv ? sh.N : sh.N / 2, n_tiles,
-                                                             tbox);
+            k_tile_box<<<(n_chunks + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M, inv ? 32 : 16,
+                                                              n_chunks, tbox);
         if (!e)
-            k_block_mask<<<(unsigned)((n_units + 127) / 128), 128, 0, st>>>(
-                ubox, tbox, n_units, sh.R, n_tiles, awords,
+            k_block_mask<<<(unsigned)((n_units + 3) / 4), 128, 0, st>>>(
+                ubox, tbox, n_units, sh.R, n_chunks, awords,
                 reinterpret_cast<unsigned long long*>(b8 + off_amask));
         e = cudaGetLastError();
     }
