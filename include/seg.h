@@ -217,6 +217,14 @@ seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launc
 seg_status seg_sync_status(const seg_atlas* atlas, void* stream);
 
 /*
+ * Limit the survivor list of the GEMM modes to `records` block records (each: 32 fibers x 32
+ * columns, 136 bytes of scratch); 0 restores the default (16 per 32 fibers + 65,536). Fibers
+ * whose survivors do not fit are rescanned exactly against the whole atlas, so results do not
+ * change; only time and scratch memory do. Not in the paper.
+ */
+seg_status seg_set_gemm_record_cap(seg_atlas* atlas, int64_t records);
+
+/*
  * Statistics of the last GEMM-mode seg_label on this atlas (read after the stream finished):
  * pairs = fibers x columns (2M directional, or M orientation-free) candidates, screened = the
  * candidates inside the (128-fiber x N-column) blocks the tensor cores computed (blocks whose

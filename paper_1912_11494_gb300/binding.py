@@ -32,6 +32,7 @@ SIGNATURES = [
     ("seg_atlas_info", ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     ("seg_label", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _P, _P, _P, _P]),
     ("seg_label_host", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _P, _P]),
+    ("seg_set_gemm_record_cap", ctypes.c_int, [_P, _I64]),
     ("seg_label_batch", ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_int, _P, _P, _P]),
     ("seg_apply_affine", ctypes.c_int, [_P, _I64, _P, _P, _P]),
     ("seg_grad", ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
@@ -241,6 +242,10 @@ def seg_grad_noalloc(atlas: Atlas, fibers, affine12, cidx, orient, grad_affine,
 
 def seg_sync_status(atlas: Atlas, stream=None):
     _check(lib().seg_sync_status(atlas.handle, _stream(stream)))
+
+
+def seg_set_gemm_record_cap(atlas: Atlas, records: int):
+    _check(lib().seg_set_gemm_record_cap(atlas.handle, int(records)))
 
 
 def seg_gemm_stats(atlas: Atlas):

@@ -1355,7 +1355,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
                     32 * 64 * MAXW);
     // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for 16
     // per 32 fibers + slack (fibers past the room are rescanned exactly)
-    const long long cap = n_pad / 32 * 16 + 65536;
+    long long cap = n_pad / 32 * 16 + 65536;
+    if (ga->cap_limit > 0 && ga->cap_limit < cap) cap = ga->cap_limit;
     const size_t elem = tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * sh.ke * elem);
     const size_t off_key = off_alpha + align256((size_t)n_pad * 4);

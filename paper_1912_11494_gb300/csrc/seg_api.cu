@@ -546,6 +546,17 @@ seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
     return SEG_OK;
 }
 
+seg_status seg_set_gemm_record_cap(seg_atlas* atlas, int64_t records) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_gemm_record_cap: atlas is NULL");
+    if (records < 0)
+        return fail(SEG_ERR_INVALID_ARG, "seg_set_gemm_record_cap: records=%lld < 0",
+                    (long long)records);
+    std::lock_guard<std::mutex> lock(atlas->mu);
+    atlas->gemm.cap_limit = records;
+    return SEG_OK;
+}
+
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
                           int64_t* overflow_fibers, int64_t* screened,
                           int64_t* point_distances) {

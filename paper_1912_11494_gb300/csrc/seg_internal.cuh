@@ -71,6 +71,7 @@ struct GemmAtlas {
     float4* ctr_sp = nullptr; // [M] centre point and theta^2 in spatial order
     long long* stats = nullptr;  // [5] pairs, survivors, overflow fibers, screened pairs,
                                  // point distances of the exact re-check
+    long long cap_limit = 0;     // caller's limit on survivor block records (0: none)
 };
 seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g,
                            cudaStream_t st);

@@ -61,6 +61,7 @@ def test_argument_errors_before_device_work(lib):
     assert lib.seg_label(None, None, 0, 0, None, None, None, None, None) == 1
     assert lib.seg_label_batch(None, 0, None, None, 0, None, None, None) == 1
     assert lib.seg_label_host(None, None, 0, 0, None, None, None) == 1
+    assert lib.seg_set_gemm_record_cap(None, 0) == 1
     assert lib.seg_grad(None, None, 0, None, None, None, None, None, None, None) == 1
     assert lib.seg_sync_status(None, None) == 1
     assert lib.seg_destroy_atlas(None) == 0

@@ -157,6 +157,9 @@ def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
         assert st["pairs"] == len(fib) * cols
         assert 0 < st["survivors"] < 0.05 * st["pairs"]  # own bundle alone is 2% at M=1,000
         assert st["overflow_fibers"] == 0
+        # every listed pair runs test1 at least; the culled blocks are never computed
+        assert st["point_distances"] >= st["survivors"]
+        assert 0 < st["screened"] <= st["pairs"] + 128 * 256 * (len(fib) // 128 + 1)
 
 
 @pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_bf16", "gemm_inv_tf32"])
@@ -200,6 +203,42 @@ def test_host_buffers_equal_device_call(dev, mode, full_size):
         binding.seg_sync_status(at)
         np.testing.assert_array_equal(h_lab.numpy(), ref_lab)
         np.testing.assert_array_equal(h_dst.numpy(), ref_dist)
+
+
+@pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_tf32"])
+def test_survivor_list_overflow_rescans_exactly(dev, mode):
+    """A survivor list capped at a few records overflows on almost every fiber; those fibers are
+    rescanned exactly against the whole atlas, and the results do not change."""
+    a = synth.make_atlas(20, per_bundle=20, seed=51)
+    fib = synth.make_subject(a, 3000, 0.8, seed=52)
+    at = make_atlas(a.centroids, a.bundle_of, a.thresholds, dev)
+    ref = run(at, fib, dev, "plain")
+    for cap in (1, 7, 100):
+        binding.seg_set_gemm_record_cap(at, cap)
+        got = run(at, fib, dev, mode)
+        st = binding.seg_gemm_stats(at)
+        assert st["overflow_fibers"] > 0
+        for x, y in zip(ref, got):
+            np.testing.assert_array_equal(x, y)
+    binding.seg_set_gemm_record_cap(at, 0)
+    run(at, fib, dev, mode)
+    assert binding.seg_gemm_stats(at)["overflow_fibers"] == 0
+    with pytest.raises(binding.SegError):
+        binding.seg_set_gemm_record_cap(at, -1)
+
+
+def test_gemm_column_limit(dev):
+    """The GEMM modes take at most 32,768 operand columns: 17,000 centroids exceed it in the
+    directional layout (2M columns) but not in the orientation-free one (M columns)."""
+    a = synth.make_atlas(850, per_bundle=20, seed=53)
+    fib = synth.make_subject(a, 500, 0.8, seed=54)
+    at = make_atlas(a.centroids, a.bundle_of, a.thresholds, dev)
+    with pytest.raises(binding.SegError):
+        run(at, fib, dev, "gemm_bf16")
+    ref = run(at, fib, dev, "plain")
+    got = run(at, fib, dev, "gemm_inv_bf16")
+    for x, y in zip(ref, got):
+        np.testing.assert_array_equal(x, y)
 
 
 def test_every_tile_shape_identical(dev, small_workload):
