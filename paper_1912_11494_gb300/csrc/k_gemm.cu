@@ -1143,10 +1143,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
 
 // Fibers whose survivors did not fit the record list: exact scan against the whole atlas (the
 // kernel returns at once when no fiber was flagged).
-__global__ void k_overflow_rescan(long long n, AtlasView at, GemmScratch g) {
-    if (*(volatile unsigned long long*)(g.cnt + 1) == 0) return;
-    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= n || g.flag[f] == 0) return;
+__device__ __noinline__ void rescan_fiber(long long f, const AtlasView& at, const GemmScratch& g) {
     const float* src = g.fs + (size_t)f * CROW;
     float a[NC];
 #pragma unroll
@@ -1158,6 +1155,13 @@ __global__ void k_overflow_rescan(long long n, AtlasView at, GemmScratch g) {
         if (exact_pair(a, at.cen + (size_t)s * CROW, bound, d2, o))
             atomicMin(g.key + f, pack_key(d2, s, o));
     }
+}
+
+__global__ void k_overflow_rescan(long long n, AtlasView at, GemmScratch g) {
+    if (*(volatile unsigned long long*)(g.cnt + 1) == 0) return;
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < n;
+         f += (long long)gridDim.x * blockDim.x)
+        if (g.flag[f]) rescan_fiber(f, at, g);
 }
 
 // Labels and distances in the caller's order.
@@ -1458,7 +1462,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_FINAL, st);
-        k_overflow_rescan<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, at, g);
+        k_overflow_rescan<<<sms * 4, 256, 0, st>>>(n, at, g);
         k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
             n, at, g, labels, dist, cidx, orient, n * (long long)cols, ga->stats);
         e = cudaGetLastError();
