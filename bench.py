@@ -473,7 +473,9 @@ def run_batch(args, world, rank, dev, dist):
         print(json.dumps({"metric": "batched subject fibers labelled/sec", "value":
                           world * total / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                          "higher_is_better": True, "scaling": "weak", "dtype": "f32",
+                          "higher_is_better": True, "scaling": "weak",
+                          "dtype": "f32" if mode == "plain" else
+                                   ("bf16+f32" if mode.endswith("bf16") else "tf32+f32"),
                           "data": "synthetic",
                           "config": {"workload": args.workload, "subjects": 16,
                                      "fibers": total, "mode": mode,

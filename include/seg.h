@@ -45,7 +45,8 @@ typedef enum {
     SEG_ERR_INVALID_ARG = 1, /* bad size, NULL where a buffer is required, bad bundle id ... */
     SEG_ERR_CUDA = 2,        /* a CUDA runtime call failed; seg_last_error() has the text */
     SEG_ERR_OOM = 3,         /* device allocation failed */
-    SEG_ERR_UNSUPPORTED = 4, /* mode or device not supported (needs sm_103a) */
+    SEG_ERR_UNSUPPORTED = 4, /* mode or device not supported (needs sm_103a), or an atlas too
+                              * large for a GEMM mode (more than 32,768 operand columns) */
     SEG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up; results of that call invalid */
     SEG_ERR_OVERFLOW = 6     /* a fixed-capacity device list overflowed and was not recovered */
 } seg_status;
@@ -63,8 +64,13 @@ typedef enum {
     /* Tensor-core prune with an orientation-free bound, then the exact test (both
      * orientations) on survivors. With c = a_10 and s_i = (a_i + a_(20-i))/2 (i < 10),
      * I(a,b) = |c_a - c_b|^2 + 2 sum_i |s_i(a) - s_i(b)|^2 <= min over orientations of the
-     * 21-point sum <= 21 d_ME^2, one column per centroid (33 features + bias). Labels and
-     * distances equal SEG_MODE_PLAIN's. Not in the paper. */
+     * 21-point sum <= 21 d_ME^2; c and s_9 merge into g = c/sqrt(2) + s_9 (a lower bound of
+     * their two terms), so one column per centroid holds 30 features + bias (K = 32). Labels
+     * and distances equal SEG_MODE_PLAIN's. Not in the paper.
+     * All GEMM modes sort the fibers by the 4 mm cell of their centre point and skip the
+     * (128-fiber, 32-column) blocks whose centre-point boxes are farther apart than every
+     * threshold of the block (d_ME >= the centre points' distance); they take at most 32,768
+     * operand columns (2M directional, M orientation-free). */
     SEG_MODE_GEMM_INV_BF16 = 3,
     SEG_MODE_GEMM_INV_TF32 = 4
 } seg_mode;
@@ -85,8 +91,8 @@ const char* seg_last_error(void);
  *   d_thresholds device float32 [B], finite and > 0, millimetres.
  *   M >= 1, B >= 1, npts must equal SEG_NPTS.
  *   out          receives the handle; release it with seg_destroy_atlas().
- * The handle holds sorted bundle-major copies of the centroids and the operands of the tensor-
- * core prune (about 0.9 KB per centroid). This call copies the bundle ids and thresholds to
+ * The handle holds sorted bundle-major copies of the centroids, a spatially ordered copy and
+ * the operands of the tensor-core prune (about 1.3 KB per centroid). This call copies the bundle ids and thresholds to
  * the host to validate them and SYNCHRONIZES `stream` before returning.
  */
 seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of,
