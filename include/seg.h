@@ -92,7 +92,7 @@ const char* seg_last_error(void);
  *   M >= 1, B >= 1, npts must equal SEG_NPTS.
  *   out          receives the handle; release it with seg_destroy_atlas().
  * The handle holds sorted bundle-major copies of the centroids, a spatially ordered copy and
- * the operands of the tensor-core prune (about 1.3 KB per centroid). This call copies the bundle ids and thresholds to
+ * the operands of the tensor-core prune (about 1.5 KB per centroid). This call copies the bundle ids and thresholds to
  * the host to validate them and SYNCHRONIZES `stream` before returning.
  */
 seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of,
