@@ -883,29 +883,6 @@ __device__ inline unsigned long long pack_key(float d2, int s, int o) {
            (unsigned)o;
 }
 
-// Exact d^2 in orientation O with progressive discarding (Section 2.3 order: centre, ends,
-// four intermediate points, the rest); false as soon as a partial maximum exceeds bound2.
-template <int O>
-__device__ inline bool exact_one(const float* a, const float* b, float bound2, float& d2) {
-    constexpr int L = NPTS - 1;
-    float m = pd2(a, CENTRE, b, CENTRE);
-    if (!(m <= bound2)) return false;
-    m = fmaxf(m, fmaxf(pd2(a, 0, b, O ? L : 0), pd2(a, L, b, O ? 0 : L)));
-    if (!(m <= bound2)) return false;
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-        const int i = test3_point(qq);
-        m = fmaxf(m, pd2(a, i, b, O ? L - i : i));
-    }
-    if (!(m <= bound2)) return false;
-#pragma unroll
-    for (int i = 1; i < L; ++i)
-        if (!is_early_point(i)) m = fmaxf(m, pd2(a, i, b, O ? L - i : i));
-    if (!(m <= bound2)) return false;
-    d2 = m;
-    return true;
-}
-
 // Exact test of the survivors, one block record per CTA at a time. The CTA copies (cp.async) the
 // block's 32 fiber rows (contiguous in the sorted copy) and the chunk's centroid rows into shared
 // memory, with theta^2 beside each centroid and each fiber's best d^2 so far; the next record's
