@@ -127,9 +127,11 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
  * SEG_HOST_CHUNKS chunks; chunk c+1 is uploaded on an internal stream while chunk c is labelled
  * (seg_label on `stream`, so the results equal seg_label's), and each chunk's results are
  * copied back on `stream`. Asynchronous: the host buffers must stay valid and unread until
- * `stream` completes. Page-locked (cudaHostAlloc) buffers let the copies overlap the labelling;
- * pageable ones work but serialise. The atlas owns the device copies (grown on demand; calls on
- * one atlas are serialised on the host).
+ * `stream` completes. The upload is not ordered after earlier work on `stream`: h_fibers must
+ * already hold the fibers when the call is made. The atlas owns two device copies used by
+ * alternate calls, so a call's upload overlaps the previous call's labelling (grown on demand;
+ * calls on one atlas are serialised on the host). Page-locked (cudaHostAlloc) buffers let the
+ * copies overlap the labelling; pageable ones work but serialise.
  */
 #define SEG_HOST_CHUNKS 4
 seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t n,

@@ -124,10 +124,13 @@ struct seg_atlas {
     unsigned* status = nullptr;
     GemmAtlas gemm{};
     ScratchArena scratch{};
-    // seg_label_host: device copies of the caller's host buffers, an internal copy stream and
-    // one event per chunk (guarded by host_mu: calls on one atlas share the buffers)
-    void* hbuf = nullptr;
-    size_t hbuf_bytes = 0;
+    // seg_label_host: two device copies of the caller's host buffers, used by alternate calls
+    // (so that a call's upload overlaps the previous call's labelling), an internal copy
+    // stream, one event per chunk and one per buffer marking its last use (guarded by
+    // host_mu)
+    void* hbuf[2] = {nullptr, nullptr};
+    size_t hbuf_bytes[2] = {0, 0};
+    int hnext = 0;
     cudaStream_t hcopy = nullptr;
     cudaEvent_t hev[SEG_HOST_CHUNKS + 2] = {};
     std::mutex host_mu;
@@ -170,7 +173,8 @@ static void free_atlas(seg_atlas* a) {
     for (cudaEvent_t ev : a->hev)
         if (ev) cudaEventDestroy(ev);
     if (a->hcopy) cudaStreamDestroy(a->hcopy);
-    cudaFree(a->hbuf);
+    cudaFree(a->hbuf[0]);
+    cudaFree(a->hbuf[1]);
     free_batch(&a->batch);
     delete a;
 }
@@ -352,24 +356,26 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)))
                 return cuda_fail(e, "seg_label_host: event");
     }
-    cudaEvent_t ev_start = a->hev[SEG_HOST_CHUNKS], ev_done = a->hev[SEG_HOST_CHUNKS + 1];
+    const int bi = a->hnext;
+    a->hnext ^= 1;
+    cudaEvent_t ev_done = a->hev[SEG_HOST_CHUNKS + bi];
     const size_t fb = ((size_t)n * NC * 4 + 255) / 256 * 256, lb = ((size_t)n * 4 + 255) / 256 * 256;
     const size_t need = fb + 2 * lb;
-    if (need > a->hbuf_bytes) {
-        // the previous call's copies and kernels may still use the old buffer
-        if ((e = cudaEventSynchronize(ev_done)) || (e = cudaFree(a->hbuf)))
+    if (need > a->hbuf_bytes[bi]) {
+        // the call before the previous one may still use the old buffer
+        if ((e = cudaEventSynchronize(ev_done)) || (e = cudaFree(a->hbuf[bi])))
             return cuda_fail(e, "seg_label_host: buffer");
-        a->hbuf = nullptr;
-        a->hbuf_bytes = 0;
-        if ((e = cudaMalloc(&a->hbuf, need))) return cuda_fail(e, "seg_label_host: buffer");
-        a->hbuf_bytes = need;
+        a->hbuf[bi] = nullptr;
+        a->hbuf_bytes[bi] = 0;
+        if ((e = cudaMalloc(&a->hbuf[bi], need))) return cuda_fail(e, "seg_label_host: buffer");
+        a->hbuf_bytes[bi] = need;
     }
-    float* d_fib = static_cast<float*>(a->hbuf);
-    int32_t* d_lab = reinterpret_cast<int32_t*>(static_cast<char*>(a->hbuf) + fb);
-    float* d_dst = reinterpret_cast<float*>(static_cast<char*>(a->hbuf) + fb + lb);
-    // the copies start after everything already queued on the caller's stream (which includes
-    // the previous call's use of the buffer)
-    if ((e = cudaEventRecord(ev_start, st)) || (e = cudaStreamWaitEvent(a->hcopy, ev_start, 0)))
+    float* d_fib = static_cast<float*>(a->hbuf[bi]);
+    int32_t* d_lab = reinterpret_cast<int32_t*>(static_cast<char*>(a->hbuf[bi]) + fb);
+    float* d_dst = reinterpret_cast<float*>(static_cast<char*>(a->hbuf[bi]) + fb + lb);
+    // the upload starts as soon as this buffer's previous use (two calls ago) has finished,
+    // which lets it overlap the previous call's labelling
+    if ((e = cudaStreamWaitEvent(a->hcopy, ev_done, 0)))
         return cuda_fail(e, "seg_label_host: ordering");
     const int chunks = n >= (1 << 21) ? SEG_HOST_CHUNKS : n >= (1 << 19) ? 2 : 1;
     const int64_t per = (n + chunks - 1) / chunks;

@@ -205,6 +205,28 @@ def test_host_buffers_equal_device_call(dev, mode, full_size):
         np.testing.assert_array_equal(h_dst.numpy(), ref_dist)
 
 
+def test_host_calls_back_to_back(dev, full_size):
+    """Consecutive seg_label_host calls with no synchronisation in between (each call's upload
+    overlaps the previous call's labelling, on alternating device buffers) all return
+    seg_label's results."""
+    atlas_np, fib = full_size
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    parts = [fib[:1_500_000], fib[1_500_000:3_000_000], fib[3_000_000:], fib[:900_001]]
+    outs = []
+    for f in parts:
+        h_fib = torch.as_tensor(np.ascontiguousarray(f)).pin_memory()
+        h_lab = torch.full((len(f),), -7, dtype=torch.int32).pin_memory()
+        h_dst = torch.full((len(f),), -7.0).pin_memory()
+        binding.seg_label_host(at, h_fib, "gemm_bf16", h_lab, h_dst)
+        outs.append((h_fib, h_lab, h_dst))
+    torch.cuda.synchronize()
+    binding.seg_sync_status(at)
+    for f, (_, h_lab, h_dst) in zip(parts, outs):
+        ref_lab, ref_dist, _, _ = run(at, f, dev, "gemm_bf16")
+        np.testing.assert_array_equal(h_lab.numpy(), ref_lab)
+        np.testing.assert_array_equal(h_dst.numpy(), ref_dist)
+
+
 @pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_tf32"])
 def test_survivor_list_overflow_rescans_exactly(dev, mode):
     """A survivor list capped at a few records overflows on almost every fiber; those fibers are
