@@ -900,6 +900,8 @@ constexpr int EX_STRIDE = 65;    // padded centroid row in shared memory: lanes 
                                  // rows never share a bank
 constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
+constexpr int EX_QLEN = 256;     // queued pairs per block; a pair past the queue is finished
+                                 // at once by the thread that tested it
 constexpr int EX_RUN = 16;       // consecutive records a CTA takes at a time
 
 // Stages of the exact test in orientation O (0: points in order, 1: reversed as in Eq. 2).
@@ -966,14 +968,14 @@ __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(EX_THREADS)
+__global__ void __launch_bounds__(EX_THREADS, 9)
 k_exact_blocks(AtlasView at, GemmScratch g) {
     __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
     __shared__ float s_cen[32 * EX_STRIDE];  // slot 64 of a row: theta^2 of its centroid
     __shared__ unsigned s_pre[32], s_best[32];
     __shared__ int s_sidx[32];               // sorted (bundle-major) index of each centroid row
-    __shared__ unsigned s_q[EX_QCAP];        // fiber | bit << 5 | direct alive << 10 | rev << 11
-    __shared__ float2 s_qm[EX_QCAP];         // partial maxima of the queued pairs
+    __shared__ unsigned s_q[EX_QLEN];        // fiber | bit << 5 | direct alive << 10 | rev << 11
+    __shared__ float2 s_qm[EX_QLEN];         // partial maxima of the queued pairs
     __shared__ unsigned s_nq;
     __shared__ unsigned long long s_first[32];  // per fiber: partial max bits << 32 | queue index
     __shared__ unsigned short s_pair[EX_QCAP];  // the block's pairs: fiber | bit << 5
@@ -1084,6 +1086,11 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             unsigned base = 0;
             if (lane == 0 && bal) base = atomicAdd(&s_nq, (unsigned)__popc(bal));
             base = __shfl_sync(0xffffffffu, base, 0);
+            if (push && base + __popc(bal & lt) >= EX_QLEN) {
+                exact_entry<INV>(ent, make_float2(md, mr), s_fib, s_cen, s_sidx, s_best,
+                                 g.key + h.x, npd);
+                push = false;
+            }
             if (push) {
                 const unsigned q = base + __popc(bal & lt);
                 s_q[q] = ent;
@@ -1104,7 +1111,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             s_q[q] = DONE_ENTRY;
         }
         __syncthreads();
-        const unsigned nq = s_nq;
+        const unsigned nq = min(s_nq, (unsigned)EX_QLEN);
         for (unsigned q = tid; q < nq; q += EX_THREADS) {
             const unsigned ent = s_q[q];
             if (ent != DONE_ENTRY)
@@ -1432,9 +1439,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
         if (inv)
-            k_exact_blocks<true><<<sms * 7, EX_THREADS, 0, st>>>(at, g);
+            k_exact_blocks<true><<<sms * 9, EX_THREADS, 0, st>>>(at, g);
         else
-            k_exact_blocks<false><<<sms * 7, EX_THREADS, 0, st>>>(at, g);
+            k_exact_blocks<false><<<sms * 9, EX_THREADS, 0, st>>>(at, g);
         e = cudaGetLastError();
     }
     if (!e) {
