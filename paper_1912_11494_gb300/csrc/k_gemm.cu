@@ -900,7 +900,7 @@ constexpr int EX_STRIDE = 65;    // padded centroid row in shared memory: lanes 
                                  // rows never share a bank
 constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
-constexpr int EX_QLEN = 256;     // queued pairs per block; a pair past the queue is finished
+constexpr int EX_QLEN = 384;     // queued pairs per block; a pair past the queue is finished
                                  // at once by the thread that tested it
 constexpr int EX_RUN = 16;       // consecutive records a CTA takes at a time
 
