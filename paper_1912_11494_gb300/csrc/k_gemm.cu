@@ -896,8 +896,14 @@ __device__ inline unsigned long long pack_key(float d2, int s, int o) {
 // exits are strict (> bound), so equal distances still reach the atomicMin of the packed key and
 // the tie rule of Algorithm 1 holds.
 constexpr int EX_THREADS = 128;
-constexpr int EX_STRIDE = 65;    // padded centroid row in shared memory: lanes on different
-                                 // rows never share a bank
+// Centroid rows in shared memory: 16 rows (directional) are copied 16 bytes at a time into
+// rows of 68 floats (two rows share a bank pattern at most); 32 rows (orientation-free) 4
+// bytes at a time into rows of 65 floats (no two rows share one).
+template <bool INV>
+struct CenRows {
+    static constexpr int STRIDE = INV ? 65 : 68;
+};
+constexpr int EX_STRIDE = 68;    // the larger centroid row stride (sizes the shared array)
 constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
 constexpr int EX_QLEN = 384;     // queued pairs per block; a pair past the queue is finished
@@ -940,7 +946,7 @@ __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float
     const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
     const int j = INV ? bit : bit >> 1;
     const float* a = s_fib + lo * FS_STRIDE;
-    const float* b = s_cen + j * EX_STRIDE;
+    const float* b = s_cen + j * CenRows<INV>::STRIDE;
     const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
     float md = mm.x, mr = mm.y, d2;
     int o;
@@ -971,7 +977,8 @@ template <bool INV>
 __global__ void __launch_bounds__(EX_THREADS, 9)
 k_exact_blocks(AtlasView at, GemmScratch g) {
     __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
-    __shared__ float s_cen[32 * EX_STRIDE];  // slot 64 of a row: theta^2 of its centroid
+    __shared__ __align__(16) float s_cen[32 * EX_STRIDE];  // slot 64 of a row: its theta^2
+    constexpr int CS = CenRows<INV>::STRIDE;
     __shared__ unsigned s_pre[32], s_best[32];
     __shared__ int s_sidx[32];               // sorted (bundle-major) index of each centroid row
     __shared__ unsigned s_q[EX_QLEN];        // fiber | bit << 5 | direct alive << 10 | rev << 11
@@ -1024,10 +1031,15 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         cur = h.x;
         const int ncen = min(INV ? 32 : 16, at.M - (int)s0);
         const float* csrc = g.cen_sp + (size_t)s0 * CROW;
-        for (int c = tid; c < ncen * CROW; c += EX_THREADS)
-            cp_async4(s_cen + (c >> 6) * EX_STRIDE + (c & 63), csrc + c);
+        if (INV) {
+            for (int c = tid; c < ncen * CROW; c += EX_THREADS)
+                cp_async4(s_cen + (c >> 6) * CS + (c & 63), csrc + c);
+        } else {
+            for (int c = tid; c < ncen * (CROW / 4); c += EX_THREADS)
+                cp_async16(s_cen + (c >> 4) * CS + 4 * (c & 15), csrc + 4 * c);
+        }
         if (tid < ncen) {
-            s_cen[tid * EX_STRIDE + 64] = __ldg(g.thr2_sp + s0 + tid);
+            s_cen[tid * CS + 64] = __ldg(g.thr2_sp + s0 + tid);
             s_sidx[tid] = __ldg(g.sp_s + s0 + tid);
         }
         if (w == 0) {
@@ -1060,7 +1072,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 const unsigned pr = s_pair[p];
                 const int lo = (int)(pr & 31u), bit = (int)(pr >> 5);
                 const float* a = s_fib + lo * FS_STRIDE;
-                const float* b = s_cen + (INV ? bit : bit >> 1) * EX_STRIDE;
+                const float* b = s_cen + (INV ? bit : bit >> 1) * CS;
                 const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
                 const float c = pd2(a, CENTRE, b, CENTRE);
                 npd += 1;
