@@ -908,6 +908,7 @@ constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned 
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
 constexpr int EX_QLEN = 384;     // queued pairs per block; a pair past the queue is finished
                                  // at once by the thread that tested it
+static_assert(EX_QLEN <= 512, "s_first keeps a queue index in nine bits");
 constexpr int EX_RUN = 16;       // consecutive records a CTA takes at a time
 
 // Stages of the exact test in orientation O (0: points in order, 1: reversed as in Eq. 2).
@@ -984,7 +985,9 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
     __shared__ unsigned s_q[EX_QLEN];        // fiber | bit << 5 | direct alive << 10 | rev << 11
     __shared__ float2 s_qm[EX_QLEN];         // partial maxima of the queued pairs
     __shared__ unsigned s_nq;
-    __shared__ unsigned long long s_first[32];  // per fiber: partial max bits << 32 | queue index
+    // per fiber: its most promising queued pair, as the partial maximum's bits with the low
+    // nine replaced by the queue index (the order only guides which pair goes first)
+    __shared__ unsigned s_first[32];
     __shared__ unsigned short s_pair[EX_QCAP];  // the block's pairs: fiber | bit << 5
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -1056,7 +1059,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 s_pair[k] = (unsigned short)(lane | ((__ffs(mm) - 1) << 5));
             const unsigned kb = (unsigned)(g.key[h.x + lane] >> 32);
             s_best[lane] = same ? min(s_best[lane], kb) : kb;
-            s_first[lane] = ~0ull;
+            s_first[lane] = ~0u;
             if (lane == 0) s_nq = 0;
         }
         cp_async_wait_all();
@@ -1110,15 +1113,14 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 // the fiber's most promising pair: smallest partial maximum of a live
                 // orientation (non-negative floats order as their bit patterns)
                 const float pm = (ent >> 10) & 1u ? ((ent >> 11) & 1u ? fminf(md, mr) : md) : mr;
-                atomicMin(s_first + (ent & 31u),
-                          ((unsigned long long)__float_as_uint(pm) << 32) | q);
+                atomicMin(s_first + (ent & 31u), (__float_as_uint(pm) & ~511u) | q);
             }
         }
         __syncthreads();
         // phase B1: each fiber's most promising pair first, so that the others meet a tight
         // bound; phase B2: the rest of the queue
-        if (tid < 32 && s_first[tid] != ~0ull) {
-            const unsigned q = (unsigned)s_first[tid];
+        if (tid < 32 && s_first[tid] != ~0u) {
+            const unsigned q = s_first[tid] & 511u;
             exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x, npd);
             s_q[q] = DONE_ENTRY;
         }
