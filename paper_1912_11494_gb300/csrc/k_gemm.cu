@@ -90,7 +90,7 @@ struct GemmScratch {
                                       // may hold survivors (a tile is computed when any of its
                                       // chunks may; the epilogue reads only those chunks)
     int awords;
-    const float* cen_sp;          // the atlas's spatial-order arrays (GemmAtlas)
+    const float4* cen_sp;         // the atlas's spatial-order arrays (GemmAtlas)
     const float* thr2_sp;
     const int* sp_s;
     uint2* hdr;                   // [cap] {first sorted fiber, first column} or EMPTY_SLOT
@@ -516,14 +516,18 @@ __global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, in
     tbox[2 * t + 1] = hi;
 }
 
-// Spatial-order copies of the atlas for the GEMM modes.
-__global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float* cen_sp,
+// Spatial-order copies of the atlas for the GEMM modes (centroid rows point-major: point i as
+// the float4 (x, y, z, 0), CROW4 per row).
+__global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float4* cen_sp,
                                float* thr2_sp, float4* ctr_sp) {
     const int c = blockIdx.x * blockDim.y + threadIdx.y;
     if (c >= at.M) return;
     const int s = sp_s[c];
     const float* src = at.cen + (size_t)s * CROW;
-    for (int k = threadIdx.x; k < CROW; k += blockDim.x) cen_sp[(size_t)c * CROW + k] = src[k];
+    for (int k = threadIdx.x; k < CROW4; k += blockDim.x)
+        cen_sp[(size_t)c * CROW4 + k] =
+            k < NPTS ? make_float4(src[3 * k], src[3 * k + 1], src[3 * k + 2], 0.0f)
+                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (threadIdx.x == 0) {
         thr2_sp[c] = at.thr2[s];
         ctr_sp[c] = make_float4(src[3 * CENTRE], src[3 * CENTRE + 1], src[3 * CENTRE + 2],
@@ -896,14 +900,14 @@ __device__ inline unsigned long long pack_key(float d2, int s, int o) {
 // exits are strict (> bound), so equal distances still reach the atomicMin of the packed key and
 // the tie rule of Algorithm 1 holds.
 constexpr int EX_THREADS = 128;
-// Centroid rows in shared memory: 16 rows (directional) are copied 16 bytes at a time into
-// rows of 68 floats (two rows share a bank pattern at most); 32 rows (orientation-free) 4
-// bytes at a time into rows of 65 floats (no two rows share one).
+// Centroid rows in shared memory, point-major as in the atlas's spatial copy (CROW4 float4 per
+// row, so one block of 16-byte copies stages them): a warp's 16-byte loads of the same point
+// of eight consecutive rows fall in eight different bank groups (21 is odd). 32 rows for
+// orientation-free columns, 16 for directional ones.
 template <bool INV>
 struct CenRows {
-    static constexpr int STRIDE = INV ? 65 : 68;
+    static constexpr int ROWS = INV ? 32 : 16;
 };
-constexpr int EX_STRIDE = 68;    // the larger centroid row stride (sizes the shared array)
 constexpr int FS_STRIDE = 68;    // fiber row in shared memory (16-byte aligned copies)
 constexpr int EX_QCAP = 32 * 32; // a block has at most 1024 pairs
 constexpr int EX_QLEN = 384;     // queued pairs per block; a pair past the queue is finished
@@ -911,25 +915,36 @@ constexpr int EX_QLEN = 384;     // queued pairs per block; a pair past the queu
 static_assert(EX_QLEN <= 512, "s_first keeps a queue index in nine bits");
 constexpr int EX_RUN = 16;       // consecutive records a CTA takes at a time
 
+// Squared distance of fiber point i (63-float row) and centroid point j (float4 row): the
+// same arithmetic as pd2, with the centroid point read in one 16-byte load.
+__device__ __forceinline__ float pd2v(const float* a, int i, const float4* b, int j) {
+    const float4 q = b[j];
+    const float dx = a[3 * i] - q.x;
+    const float dy = a[3 * i + 1] - q.y;
+    const float dz = a[3 * i + 2] - q.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
 // Stages of the exact test in orientation O (0: points in order, 1: reversed as in Eq. 2).
 template <int O>
-__device__ __forceinline__ float ends2(const float* a, const float* b) {
+__device__ __forceinline__ float ends2(const float* a, const float4* b) {
     constexpr int L = NPTS - 1;
-    return fmaxf(pd2(a, 0, b, O ? L : 0), pd2(a, L, b, O ? 0 : L));
+    return fmaxf(pd2v(a, 0, b, O ? L : 0), pd2v(a, L, b, O ? 0 : L));
 }
 template <int O>
-__device__ __forceinline__ float mid4(const float* a, const float* b, float m) {
+__device__ __forceinline__ float mid4(const float* a, const float4* b, float m) {
     constexpr int L = NPTS - 1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) m = fmaxf(m, pd2(a, test3_point(q), b, O ? L - test3_point(q) : test3_point(q)));
+    for (int q = 0; q < 4; ++q)
+        m = fmaxf(m, pd2v(a, test3_point(q), b, O ? L - test3_point(q) : test3_point(q)));
     return m;
 }
 template <int O>
-__device__ __forceinline__ float rest17(const float* a, const float* b, float m) {
+__device__ __forceinline__ float rest17(const float* a, const float4* b, float m) {
     constexpr int L = NPTS - 1;
 #pragma unroll
     for (int i = 1; i < L; ++i)
-        if (!is_early_point(i)) m = fmaxf(m, pd2(a, i, b, O ? L - i : i));
+        if (!is_early_point(i)) m = fmaxf(m, pd2v(a, i, b, O ? L - i : i));
     return m;
 }
 
@@ -941,14 +956,14 @@ constexpr unsigned DONE_ENTRY = 0xFFFFFFFFu;  // queue entry already tested
 // already merged.
 template <bool INV>
 __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float* s_fib,
-                                            const float* s_cen, const int* s_sidx,
-                                            unsigned* s_best, unsigned long long* key,
-                                            unsigned& npd) {
+                                            const float4* s_cen, const float* s_thr,
+                                            const int* s_sidx, unsigned* s_best,
+                                            unsigned long long* key, unsigned& npd) {
     const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
     const int j = INV ? bit : bit >> 1;
     const float* a = s_fib + lo * FS_STRIDE;
-    const float* b = s_cen + j * CenRows<INV>::STRIDE;
-    const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
+    const float4* b = s_cen + j * CROW4;
+    const float bound = fminf(s_thr[j], __uint_as_float(s_best[lo]));
     float md = mm.x, mr = mm.y, d2;
     int o;
     bool pass;
@@ -978,8 +993,8 @@ template <bool INV>
 __global__ void __launch_bounds__(EX_THREADS, 9)
 k_exact_blocks(AtlasView at, GemmScratch g) {
     __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
-    __shared__ __align__(16) float s_cen[32 * EX_STRIDE];  // slot 64 of a row: its theta^2
-    constexpr int CS = CenRows<INV>::STRIDE;
+    __shared__ __align__(16) float4 s_cen[CenRows<INV>::ROWS * CROW4];
+    __shared__ float s_thr[32];              // theta^2 of each centroid row
     __shared__ unsigned s_pre[32], s_best[32];
     __shared__ int s_sidx[32];               // sorted (bundle-major) index of each centroid row
     __shared__ unsigned s_q[EX_QLEN];        // fiber | bit << 5 | direct alive << 10 | rev << 11
@@ -1032,17 +1047,12 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 cp_async16(s_fib + (c >> 4) * FS_STRIDE + 4 * (c & 15), fsrc + 4 * c);
         }
         cur = h.x;
-        const int ncen = min(INV ? 32 : 16, at.M - (int)s0);
-        const float* csrc = g.cen_sp + (size_t)s0 * CROW;
-        if (INV) {
-            for (int c = tid; c < ncen * CROW; c += EX_THREADS)
-                cp_async4(s_cen + (c >> 6) * CS + (c & 63), csrc + c);
-        } else {
-            for (int c = tid; c < ncen * (CROW / 4); c += EX_THREADS)
-                cp_async16(s_cen + (c >> 4) * CS + 4 * (c & 15), csrc + 4 * c);
-        }
+        const int ncen = min(CenRows<INV>::ROWS, at.M - (int)s0);
+        const float4* csrc = g.cen_sp + (size_t)s0 * CROW4;
+        for (int c = tid; c < ncen * CROW4; c += EX_THREADS)
+            cp_async16(reinterpret_cast<float*>(s_cen + c), reinterpret_cast<const float*>(csrc + c));
         if (tid < ncen) {
-            s_cen[tid * CS + 64] = __ldg(g.thr2_sp + s0 + tid);
+            s_thr[tid] = __ldg(g.thr2_sp + s0 + tid);
             s_sidx[tid] = __ldg(g.sp_s + s0 + tid);
         }
         if (w == 0) {
@@ -1075,9 +1085,10 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 const unsigned pr = s_pair[p];
                 const int lo = (int)(pr & 31u), bit = (int)(pr >> 5);
                 const float* a = s_fib + lo * FS_STRIDE;
-                const float* b = s_cen + (INV ? bit : bit >> 1) * CS;
-                const float bound = fminf(b[64], __uint_as_float(s_best[lo]));
-                const float c = pd2(a, CENTRE, b, CENTRE);
+                const int j = INV ? bit : bit >> 1;
+                const float4* b = s_cen + j * CROW4;
+                const float bound = fminf(s_thr[j], __uint_as_float(s_best[lo]));
+                const float c = pd2v(a, CENTRE, b, CENTRE);
                 npd += 1;
                 if (c <= bound) {
                     bool ad, ar = false;
@@ -1102,7 +1113,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             if (lane == 0 && bal) base = atomicAdd(&s_nq, (unsigned)__popc(bal));
             base = __shfl_sync(0xffffffffu, base, 0);
             if (push && base + __popc(bal & lt) >= EX_QLEN) {
-                exact_entry<INV>(ent, make_float2(md, mr), s_fib, s_cen, s_sidx, s_best,
+                exact_entry<INV>(ent, make_float2(md, mr), s_fib, s_cen, s_thr, s_sidx, s_best,
                                  g.key + h.x, npd);
                 push = false;
             }
@@ -1121,7 +1132,8 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         // bound; phase B2: the rest of the queue
         if (tid < 32 && s_first[tid] != ~0u) {
             const unsigned q = s_first[tid] & 511u;
-            exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x, npd);
+            exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_thr, s_sidx, s_best, g.key + h.x,
+                             npd);
             s_q[q] = DONE_ENTRY;
         }
         __syncthreads();
@@ -1129,7 +1141,8 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         for (unsigned q = tid; q < nq; q += EX_THREADS) {
             const unsigned ent = s_q[q];
             if (ent != DONE_ENTRY)
-                exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_sidx, s_best, g.key + h.x, npd);
+                exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_thr, s_sidx, s_best, g.key + h.x,
+                                 npd);
         }
         __syncthreads();  // the buffers are refilled for the next record
     }
@@ -1286,7 +1299,7 @@ seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g
         (e = cudaMemsetAsync(g->stats, 0, 5 * sizeof(long long), st)))
         return cuda_fail(e, "gemm stats");
     if ((e = cudaMalloc(&g->sp_s, (size_t)at.M * sizeof(int))) ||
-        (e = cudaMalloc(&g->cen_sp, (size_t)at.M * CROW * sizeof(float))) ||
+        (e = cudaMalloc(&g->cen_sp, (size_t)at.M * CROW4 * sizeof(float4))) ||
         (e = cudaMalloc(&g->thr2_sp, (size_t)at.M * sizeof(float))) ||
         (e = cudaMalloc(&g->ctr_sp, (size_t)at.M * sizeof(float4))))
         return cuda_fail(e, "gemm spatial order");
@@ -1453,7 +1466,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
         if (inv)
-            k_exact_blocks<true><<<sms * 9, EX_THREADS, 0, st>>>(at, g);
+            k_exact_blocks<true><<<sms * 8, EX_THREADS, 0, st>>>(at, g);
         else
             k_exact_blocks<false><<<sms * 9, EX_THREADS, 0, st>>>(at, g);
         e = cudaGetLastError();

@@ -11,6 +11,7 @@ namespace seg {
 constexpr int NPTS = SEG_NPTS;   // 21 points per fiber (Section 2.3 resampling)
 constexpr int NC = NPTS * 3;     // 63 coordinates
 constexpr int CROW = 64;         // padded centroid row (floats) in the sorted copy
+constexpr int CROW4 = NPTS;      // point-major centroid row: one float4 (x, y, z, 0) per point
 constexpr int CENTRE = 10;       // test1 point; maps to itself under reversal (20 - 10)
 
 // Device status word bits (sticky until seg_sync_status reads them).

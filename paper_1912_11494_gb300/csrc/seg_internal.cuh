@@ -66,7 +66,7 @@ struct GemmAtlas {
     // Columns follow the spatial order of the centroids (Morton order of the centre point's
     // 4 mm cell): spatial position c holds sorted centroid sp_s[c]; directional columns 2c, 2c+1.
     int* sp_s = nullptr;      // [M]
-    float* cen_sp = nullptr;  // [M][64] centroid rows in spatial order
+    float4* cen_sp = nullptr; // [M][21] centroid rows in spatial order, point-major
     float* thr2_sp = nullptr; // [M] theta^2 in spatial order
     float4* ctr_sp = nullptr; // [M] centre point and theta^2 in spatial order
     long long* stats = nullptr;  // [5] pairs, survivors, overflow fibers, screened pairs,
