@@ -9,7 +9,8 @@
  *
  * Conventions shared by every entry point:
  *  - Coordinates are float32 millimetres, fibers and centroids laid out [count][21][3]
- *    (point-major, xyz innermost), C-contiguous, 4-byte aligned.
+ *    (point-major, xyz innermost), C-contiguous, 4-byte aligned (a float or int32 buffer
+ *    that is not returns SEG_ERR_INVALID_ARG).
  *  - Pointers named d_* are device memory owned by the caller; h_* are host memory owned by
  *    the caller. The library keeps no pointer to caller memory after a call returns, except
  *    that asynchronous work queued on `stream` reads and writes it until the stream reaches it.

@@ -60,6 +60,9 @@ Profiler::~Profiler() {
 
 namespace {
 
+// float and int32 buffers are read and written as 4-byte words
+bool unaligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) != 0; }
+
 // Sorted copy of the atlas: row s of the output is caller centroid perm[s].
 __global__ void k_prep_atlas(const float* __restrict__ cen, const int* __restrict__ bundle_of,
                              const float* __restrict__ thr, const int* __restrict__ perm, int M,
@@ -320,6 +323,8 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld < 0", (long long)n);
     if (n > 0 && (!d_fibers || !d_labels))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: NULL fibers or labels");
+    if (unaligned4(d_fibers) || unaligned4(d_labels) || unaligned4(d_dist) || unaligned4(d_cidx))
+        return fail(SEG_ERR_INVALID_ARG, "seg_label: a buffer is not 4-byte aligned");
     if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_GEMM_INV_TF32)
         return fail(SEG_ERR_INVALID_ARG, "seg_label: unknown mode %d", (int)mode);
     if (n == 0) return SEG_OK;
@@ -416,6 +421,10 @@ seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* c
             return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: count[%d] < 0", s);
         if (h_counts[s] > 0 && (!h_fibers[s] || !h_labels[s]))
             return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: NULL buffer for subject %d", s);
+        if (unaligned4(h_fibers[s]) || unaligned4(h_labels[s]) ||
+            (h_dist && unaligned4(h_dist[s])))
+            return fail(SEG_ERR_INVALID_ARG,
+                        "seg_label_batch: a buffer of subject %d is not 4-byte aligned", s);
     }
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
     ProfScope ps(&a->prof, PROF_BATCH, (cudaStream_t)stream);
@@ -431,6 +440,8 @@ seg_status seg_apply_affine(const float* d_in, int64_t n, const double* h_affine
     if (!h_affine12) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: NULL affine");
     if (n == 0) return SEG_OK;
     if (!d_in || !d_out) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: NULL buffer");
+    if (unaligned4(d_in) || unaligned4(d_out))
+        return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: buffer not 4-byte aligned");
     return apply_affine_launch(d_in, n, h_affine12, d_out, (cudaStream_t)stream);
 }
 
@@ -445,6 +456,8 @@ seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
         return fail(SEG_ERR_INVALID_ARG, "seg_grad: NULL affine or gradient buffer");
     if (n > 0 && (!d_fibers || !d_cidx || !d_orient))
         return fail(SEG_ERR_INVALID_ARG, "seg_grad: NULL fibers, cidx or orient");
+    if (unaligned4(d_fibers) || unaligned4(d_cidx))
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad: fibers or cidx not 4-byte aligned");
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
     ProfScope ps(&a->prof, PROF_GRAD, (cudaStream_t)stream);
     return grad_launch(a->view, a->inv_perm, &a->scratch, &a->mu, d_fibers, n, h_affine12,
@@ -494,6 +507,8 @@ seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64
         return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: NULL affine or gradient buffer");
     if (n > 0 && (!d_fibers || !d_cidx || !d_orient))
         return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: NULL fibers, cidx or orient");
+    if (unaligned4(d_fibers) || unaligned4(d_cidx))
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: fibers or cidx not 4-byte aligned");
     return grad_noalloc_launch(atlas->view, atlas->inv_perm, d_fibers, n, h_affine12, d_cidx,
                                d_orient, d_grad_affine12, d_grad_centroids, d_cost,
                                (cudaStream_t)stream);

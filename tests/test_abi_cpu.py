@@ -68,3 +68,8 @@ def test_argument_errors_before_device_work(lib):
     assert lib.seg_apply_affine(None, -1, None, None, None) == 1
     assert lib.seg_apply_affine(None, 0, None, None, None) == 1
     assert lib.seg_gemm_stats(None, None, None, None, None, None) == 1
+    # a float buffer that is not 4-byte aligned is refused before it is touched
+    aff = (ctypes.c_double * 12)()
+    assert lib.seg_apply_affine(ctypes.c_void_p(0x1002), 1, aff, ctypes.c_void_p(0x2000),
+                                None) == 1
+    assert b"aligned" in lib.seg_last_error()

@@ -184,6 +184,37 @@ def test_gemm_locality_order_extremes(dev, mode):
 
 
 @pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "gemm_inv_tf32"])
+def test_fibers_at_any_4_byte_offset(dev, mode):
+    """A fiber array starting 0, 4, 8 or 12 bytes past a 16-byte boundary (a view into a larger
+    buffer) gives the same results, its first and last fibers included; a pointer off the
+    4-byte grid is refused before any work."""
+    import ctypes
+    a = synth.make_atlas(25, per_bundle=20, seed=61)
+    fib = synth.make_subject(a, 1537, 0.9, seed=62)
+    fib[0] = a.centroids[3] + 0.5      # first and last fibers next to a centroid, so their
+    fib[-1] = a.centroids[17][::-1]    # pairs reach the exact re-check
+    at = make_atlas(a.centroids, a.bundle_of, a.thresholds, dev)
+    ref = run(at, fib, dev, "plain")
+    assert ref[0][0] >= 0 and ref[0][-1] >= 0
+    n = len(fib)
+    for off in range(4):
+        buf = torch.zeros(n * 63 + 8, dtype=torch.float32, device=dev)
+        buf[off:off + n * 63] = torch.as_tensor(fib.reshape(-1), device=dev)
+        f = buf[off:off + n * 63].view(n, 21, 3)
+        assert f.data_ptr() % 16 == 4 * off
+        lab, dist, cidx, orient = binding.label(at, f, mode)
+        binding.seg_sync_status(at)
+        for x, y in zip(ref, (lab.cpu().numpy(), dist.cpu().numpy(), cidx.cpu().numpy(),
+                              orient.cpu().numpy())):
+            np.testing.assert_array_equal(x, y)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    rc = binding.lib().seg_label(at.handle, ctypes.c_void_p(buf.data_ptr() + 2), n,
+                                 binding.MODES[mode], ctypes.c_void_p(lab.data_ptr()), None,
+                                 None, None, None)
+    assert rc == 1 and b"aligned" in binding.lib().seg_last_error()
+
+
+@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "gemm_inv_tf32"])
 def test_host_buffers_equal_device_call(dev, mode, full_size):
     """seg_label_host (chunked upload overlapping the labelling) returns seg_label's results,
     for 4 chunks (the full subject, pinned buffers), 2 chunks and 1 chunk (pageable buffers),
