@@ -218,25 +218,17 @@ __global__ void k_prep_b(AtlasView at, const int* sp_s, int fmt, int cols, int c
 // ---- locality order --------------------------------------------------------------------------
 // Subjects arrive in arbitrary order, so the 32 fibers a warp of the screen reads would have
 // unrelated survivor columns. A counting sort on the cell of the centre point (4 mm cells, a 64^3
-// grid around the atlas centre, cells in Morton order) groups fibers that lie close together;
-// every later kernel addresses fibers by their sorted position and reads the caller's row
-// through perm[]. Results do not depend on the order (each fiber's key is its own minimum).
-constexpr int GRID_BITS = 6;                       // cells per axis = 64
-constexpr int NBINS = 1 << (3 * GRID_BITS);        // 262,144 cells
+// grid around the atlas centre, cells along a Hilbert curve: hilbert_index3) groups fibers that
+// lie close together; every later kernel addresses fibers by their sorted position and reads the
+// caller's row through perm[]. Results do not depend on the order (each fiber's key is its own
+// minimum).
+constexpr int NBINS = 1 << (3 * LOC_BITS);         // 262,144 cells
 constexpr int SCAN_BLOCK = 1024;                   // bins scanned per block
 constexpr int NTOP = NBINS / SCAN_BLOCK;           // 256 block totals
-constexpr float CELL_MM = 4.0f;
-
-__device__ inline unsigned spread3(unsigned v) {   // 6 bits -> every third bit
-    unsigned r = 0;
-#pragma unroll
-    for (int b = 0; b < GRID_BITS; ++b) r |= ((v >> b) & 1u) << (3 * b);
-    return r;
-}
 
 __device__ inline unsigned cell_of(float v, float c0) {
-    const float t = floorf((v - c0) * (1.0f / CELL_MM)) + (float)(1 << (GRID_BITS - 1));
-    return t >= 0.0f ? (unsigned)fminf(t, (float)((1 << GRID_BITS) - 1)) : 0u;  // NaN -> 0
+    const float t = floorf((v - c0) * (1.0f / LOC_CELL_MM)) + (float)(1 << (LOC_BITS - 1));
+    return t >= 0.0f ? (unsigned)fminf(t, (float)((1 << LOC_BITS) - 1)) : 0u;  // NaN -> 0
 }
 
 __global__ void k_bin_count(const float* __restrict__ fib, long long n, AtlasView at,
@@ -244,9 +236,8 @@ __global__ void k_bin_count(const float* __restrict__ fib, long long n, AtlasVie
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float* c = fib + i * NC + 3 * CENTRE;
-    const unsigned b = spread3(cell_of(__ldg(c), at.c0x)) |
-                       (spread3(cell_of(__ldg(c + 1), at.c0y)) << 1) |
-                       (spread3(cell_of(__ldg(c + 2), at.c0z)) << 2);
+    const unsigned b = hilbert_index3(cell_of(__ldg(c), at.c0x), cell_of(__ldg(c + 1), at.c0y),
+                                      cell_of(__ldg(c + 2), at.c0z));
     bin[i] = b;
     atomicAdd(hist + b, 1u);
 }

@@ -230,21 +230,22 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
     for (int c = 0; c < M; ++c)
         for (int r = 0; r < 3; ++r) c0[r] += hc[(size_t)c * NC + 3 * CENTRE + r];
     for (int r = 0; r < 3; ++r) c0[r] = std::round(c0[r] / M);
-    // Spatial order of the sorted centroids for the tensor-core prune: Morton order of the 4 mm
-    // cell of the centre point (the grid the GEMM modes also sort fibers on), so that a tile of
-    // consecutive columns covers a compact region. sp[c] = sorted index at spatial position c.
+    // Spatial order of the sorted centroids for the tensor-core prune: the Hilbert-curve
+    // position of the centre point's 4 mm cell (the grid the GEMM modes also sort fibers on), so
+    // that a tile of consecutive columns covers a compact region. sp[c] = sorted index at
+    // spatial position c.
     std::vector<int32_t> sp(M);
     {
         std::vector<std::pair<uint32_t, int32_t>> key(M);
         for (int s = 0; s < M; ++s) {
-            uint32_t k = 0;
+            uint32_t cell[3];
             for (int r = 0; r < 3; ++r) {
                 const double v = hc[(size_t)perm[s] * NC + 3 * CENTRE + r];
-                double t = std::floor((v - c0[r]) / 4.0) + 32.0;
-                const uint32_t cell = t < 0.0 ? 0u : t > 63.0 ? 63u : (uint32_t)t;
-                for (int b = 0; b < 6; ++b) k |= ((cell >> b) & 1u) << (3 * b + r);
+                const double t = std::floor((v - c0[r]) / LOC_CELL_MM) + (1 << (LOC_BITS - 1));
+                const double top = (1 << LOC_BITS) - 1;
+                cell[r] = t >= 0.0 ? (uint32_t)(t < top ? t : top) : 0u;  // NaN -> 0
             }
-            key[s] = {k, s};
+            key[s] = {hilbert_index3(cell[0], cell[1], cell[2]), s};
         }
         std::stable_sort(key.begin(), key.end(),
                          [](const auto& x, const auto& y) { return x.first < y.first; });

@@ -20,6 +20,43 @@ constexpr unsigned ST_OVERFLOW = 2u;
 
 constexpr int MPAD = 2048;    // the sorted atlas is padded to a multiple of this many centroids
 
+// Locality order of the GEMM modes: the centre point's cell (LOC_CELL_MM cells, 2^LOC_BITS per
+// axis around the atlas centre, clamped) taken along a three-dimensional Hilbert curve, whose
+// consecutive cells always share a face, so that a run of consecutive positions covers a compact
+// region. The fibers are counting-sorted on it on the device and the centroid columns ordered
+// by it on the host.
+constexpr int LOC_BITS = 6;          // 64 cells per axis
+constexpr float LOC_CELL_MM = 4.0f;
+
+// Position of cell (x, y, z), each in [0, 2^LOC_BITS), along the Hilbert curve, in
+// [0, 2^(3 LOC_BITS)). Skilling's transform (J. Skilling, "Programming the Hilbert curve", AIP
+// Conf. Proc. 707, 2004): undo the excess rotations and reflections level by level, Gray-code
+// across the axes, then interleave the bits (bit b of axis i goes to bit 3b + 2 - i).
+__host__ __device__ inline uint32_t hilbert_index3(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t X[3] = {x, y, z};
+    for (uint32_t Q = 1u << (LOC_BITS - 1); Q > 1u; Q >>= 1) {
+        const uint32_t P = Q - 1u;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;                               // reflect the lower bits of axis 0
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;    // swap the lower bits of 0 and i
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = 1u << (LOC_BITS - 1); Q > 1u; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1u;
+    uint32_t h = 0;
+    for (int b = 0; b < LOC_BITS; ++b)
+        for (int i = 0; i < 3; ++i) h |= (((X[i] ^ t) >> b) & 1u) << (3 * b + 2 - i);
+    return h;
+}
+
 // Read-only device view of an atlas, sorted bundle-major (the visiting order of Algorithm 1).
 struct AtlasView {
     int M;                      // centroids
