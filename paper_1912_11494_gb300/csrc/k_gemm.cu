@@ -456,20 +456,39 @@ __device__ __forceinline__ int next_tile(unsigned long long& bits, int wd) {
     return wd * (64 / CPT) + gi;
 }
 
-struct UnitMask {
-    unsigned long long w[MAXW];
-    __device__ void load(const GemmScratch& g, long long u, long long n_units) {
-#pragma unroll
-        for (int k = 0; k < MAXW; ++k)
-            w[k] = (u < n_units && k < g.awords) ? __ldg(g.amask + u * g.awords + k) : 0ull;
+// The chunk masks of the units one thread of the screen visits (u, u + grid, ...), copied into
+// a private ring of three shared-memory slots two units ahead with cp.async (one commit group
+// per unit), so that the thread never stalls on the load of a unit's mask.
+struct MaskRing {
+    unsigned long long (*s)[MAXW];  // [3][MAXW]; words past awords stay zero
+    int slot = 0;                   // slot of the current unit
+    __device__ void init(unsigned long long (*ring)[MAXW], const GemmScratch& g, long long u0,
+                         long long n_units) {
+        s = ring;
+        for (int i = 0; i < 3; ++i)
+            for (int k = g.awords; k < MAXW; ++k) s[i][k] = 0ull;
+        issue(g, u0, n_units, 0);
+        issue(g, u0 + gridDim.x, n_units, 1);
     }
-    __device__ bool any() const {
-        unsigned long long a = 0;
-#pragma unroll
-        for (int k = 0; k < MAXW; ++k) a |= w[k];
-        return a != 0;
+    __device__ void issue(const GemmScratch& g, long long u, long long n_units, int i) {
+        if (u < n_units)
+            for (int k = 0; k < g.awords; ++k) cp_async8(&s[i][k], g.amask + u * g.awords + k);
+        cp_async_commit();
     }
+    // the current unit u's words (its copies have landed); the copies for u + 2 grid start
+    __device__ const unsigned long long* enter(const GemmScratch& g, long long u,
+                                               long long n_units) {
+        issue(g, u + 2 * (long long)gridDim.x, n_units, slot == 0 ? 2 : slot - 1);
+        cp_async_wait_group<2>();
+        return s[slot];
+    }
+    __device__ void leave() { slot = slot == 2 ? 0 : slot + 1; }
 };
+__device__ inline bool any_word(const unsigned long long* w, int words) {
+    unsigned long long a = 0;
+    for (int k = 0; k < words; ++k) a |= w[k];
+    return a != 0;
+}
 
 // Active-chunk masks: one thread per work unit of R x 128 sorted fibers, one bit per 32-column
 // chunk.
@@ -619,6 +638,7 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint64_t* mma_done = acc_full + 2 * C::NACC;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
+    __shared__ unsigned long long s_umask[2][3][MAXW];  // mask rings of warps 0 and 1
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -658,12 +678,16 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         uint32_t a_used = 0, a_par = 0;
         long long it = 0;
         bool ok = true;
-        UnitMask um, nm;
-        um.load(g, blockIdx.x, n_units);
+        MaskRing ring;
+        ring.init(s_umask[0], g, blockIdx.x, n_units);
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            nm.load(g, u + gridDim.x, n_units);  // next unit's mask, loaded ahead
-            if (!um.any()) {                      // every block of the unit is culled
-                um = nm;
+            const unsigned long long* um = ring.enter(g, u, n_units);
+            if (u + gridDim.x < n_units)  // the next unit's fiber tile is brought into L2
+                bulk_prefetch_l2(static_cast<const unsigned char*>(g.a) +
+                                     (size_t)(u + gridDim.x) * R * C::A_TILE,
+                                 (uint32_t)(R * C::A_TILE));
+            if (!any_word(um, g.awords)) {  // every block of the unit is culled
+                ring.leave();
                 continue;
             }
             const int ab = ABUF == 2 ? (int)(it & 1) : 0;
@@ -680,8 +704,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 kr * (C::REGB / C::ELEM),
                                 (int)((u * R + r) * 128), a_full + ab);
 #pragma unroll 1
-            for (int wd = 0; wd < MAXW && ok; ++wd)
-            for (unsigned long long bits = um.w[wd]; bits;) {
+            for (int wd = 0; wd < g.awords && ok; ++wd)
+            for (unsigned long long bits = um[wd]; bits;) {
                 const int t = next_tile<CPT>(bits, wd);
                 if (!W.wait(b_empty + stage, ((b_phase >> stage) & 1u) ^ 1u)) {
                     ok = false;
@@ -697,8 +721,9 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 stage = stage + 1 == S ? 0 : stage + 1;
             }
             ++it;
-            um = nm;
+            ring.leave();
         }
+        cp_async_wait_all();  // the ring's last copies
         if (s_abort) {
             // copies this thread issued may still be landing: wait for each buffer's last load
             // (b_phase bit s flipped once per load, so its complement is the last load's parity)
@@ -715,12 +740,12 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         long long it = 0, tile = 0;
         bool ok = true;
         long long active = 0;
-        UnitMask um, nm;
-        um.load(g, blockIdx.x, n_units);
+        MaskRing ring;
+        ring.init(s_umask[1], g, blockIdx.x, n_units);
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            nm.load(g, u + gridDim.x, n_units);
-            if (!um.any()) {
-                um = nm;
+            const unsigned long long* um = ring.enter(g, u, n_units);
+            if (!any_word(um, g.awords)) {
+                ring.leave();
                 continue;
             }
             const int ab = ABUF == 2 ? (int)(it & 1) : 0;
@@ -730,8 +755,8 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const uint64_t ad_unit =
                 make_sdesc<C::REGB>(smem_u32(smem + C::A_OFF + ab * R * C::A_TILE));
 #pragma unroll 1
-            for (int wd = 0; wd < MAXW && ok; ++wd)
-            for (unsigned long long bits = um.w[wd]; bits;) {
+            for (int wd = 0; wd < g.awords && ok; ++wd)
+            for (unsigned long long bits = um[wd]; bits;) {
                 (void)next_tile<CPT>(bits, wd);
                 ++active;
                 const int cb = (int)(tile % C::NACC);
@@ -772,8 +797,9 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             mma_commit(a_empty + ab);
             ++it;
-            um = nm;
+            ring.leave();
         }
+        cp_async_wait_all();  // the ring's last copies
         atomicAdd(g.cnt + 3, (unsigned long long)(active * R * 128 * N));
         // every MMA and every commit above has completed once this arrives
         mma_commit(mma_done);
@@ -791,15 +817,26 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         unsigned long long surv = 0;
         long long tile = 0;
         bool ok = true;
+        // each unit's alpha values and mask words (one per lane, handed out by shuffles) are
+        // loaded one unit ahead, so that a unit never starts on a memory round trip
+        float aln[4];
+        unsigned long long mwn;
+        auto load_unit = [&](long long u) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                aln[r] = r < R && u < n_units
+                             ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane)
+                             : INFINITY;
+            mwn = u < n_units && lane < g.awords ? __ldg(g.amask + u * g.awords + lane) : 0ull;
+        };
+        load_unit(blockIdx.x);
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
             float al[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                al[r] = r < R ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane) : INFINITY;
+            for (int r = 0; r < 4; ++r) al[r] = aln[r];
+            const unsigned long long mword = mwn;
+            load_unit(u + gridDim.x);
             const unsigned fib0 = (unsigned)(u * R * 128 + 32 * q + lane);
-            // the unit's mask words, one per lane, handed out by shuffles
-            const unsigned long long mword =
-                lane < g.awords ? __ldg(g.amask + u * g.awords + lane) : 0ull;
             for (int wd = 0; wd < g.awords && ok; ++wd)
             for (unsigned long long bits = __shfl_sync(0xffffffffu, mword, wd); bits;) {
                 const unsigned long long word = bits;
