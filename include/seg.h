@@ -68,7 +68,8 @@ typedef enum {
      * 21-point sum <= 21 d_ME^2; c and s_9 merge into g = c/sqrt(2) + s_9 (a lower bound of
      * their two terms), so one column per centroid holds 30 features + bias (K = 32). Labels
      * and distances equal SEG_MODE_PLAIN's. Not in the paper.
-     * All GEMM modes sort the fibers by the 4 mm cell of their centre point and skip the
+     * All GEMM modes sort the fibers by the 2 mm cell of their centre point (cells along a
+     * Hilbert curve; the centroid columns follow the same order) and skip the
      * (128-fiber, 32-column) blocks whose centre-point boxes are farther apart than every
      * threshold of the block (d_ME >= the centre points' distance); they take at most 32,768
      * operand columns (2M directional, M orientation-free). */

@@ -17,7 +17,7 @@
 // is rounded upward, and the slacks cover FP32 norms, the centring and the exact test's own
 // rounding (rho). Every pair the exact FP32 test would accept therefore survives the prune.
 //
-// Kernels. A counting sort orders the fibers by the 4 mm cell of their centre point, so that
+// Kernels. A counting sort orders the fibers by the 2 mm cell of their centre point, so that
 // the 32 fibers of a warp have nearly the same survivors. The fiber operand is written in that
 // order. The screen is a persistent CTA per SM, warp-specialised: warp 0 issues TMA loads (R
 // fiber tiles of 128 rows per work unit, double-buffered, and a ring of S centroid tiles of N
@@ -217,14 +217,14 @@ __global__ void k_prep_b(AtlasView at, const int* sp_s, int fmt, int cols, int c
 
 // ---- locality order --------------------------------------------------------------------------
 // Subjects arrive in arbitrary order, so the 32 fibers a warp of the screen reads would have
-// unrelated survivor columns. A counting sort on the cell of the centre point (4 mm cells, a 64^3
+// unrelated survivor columns. A counting sort on the cell of the centre point (2 mm cells, a 128^3
 // grid around the atlas centre, cells along a Hilbert curve: hilbert_index3) groups fibers that
 // lie close together; every later kernel addresses fibers by their sorted position and reads the
 // caller's row through perm[]. Results do not depend on the order (each fiber's key is its own
 // minimum).
-constexpr int NBINS = 1 << (3 * LOC_BITS);         // 262,144 cells
+constexpr int NBINS = 1 << (3 * LOC_BITS);         // 2,097,152 cells
 constexpr int SCAN_BLOCK = 1024;                   // bins scanned per block
-constexpr int NTOP = NBINS / SCAN_BLOCK;           // 256 block totals
+constexpr int NTOP = NBINS / SCAN_BLOCK;           // 2,048 block totals
 
 __device__ inline unsigned cell_of(float v, float c0) {
     const float t = floorf((v - c0) * (1.0f / LOC_CELL_MM)) + (float)(1 << (LOC_BITS - 1));

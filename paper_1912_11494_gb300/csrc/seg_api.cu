@@ -231,7 +231,7 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
         for (int r = 0; r < 3; ++r) c0[r] += hc[(size_t)c * NC + 3 * CENTRE + r];
     for (int r = 0; r < 3; ++r) c0[r] = std::round(c0[r] / M);
     // Spatial order of the sorted centroids for the tensor-core prune: the Hilbert-curve
-    // position of the centre point's 4 mm cell (the grid the GEMM modes also sort fibers on), so
+    // position of the centre point's cell (the grid the GEMM modes also sort fibers on), so
     // that a tile of consecutive columns covers a compact region. sp[c] = sorted index at
     // spatial position c.
     std::vector<int32_t> sp(M);

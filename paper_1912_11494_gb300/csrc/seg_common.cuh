@@ -25,8 +25,8 @@ constexpr int MPAD = 2048;    // the sorted atlas is padded to a multiple of thi
 // consecutive cells always share a face, so that a run of consecutive positions covers a compact
 // region. The fibers are counting-sorted on it on the device and the centroid columns ordered
 // by it on the host.
-constexpr int LOC_BITS = 6;          // 64 cells per axis
-constexpr float LOC_CELL_MM = 4.0f;
+constexpr int LOC_BITS = 7;          // 128 cells per axis
+constexpr float LOC_CELL_MM = 2.0f;  // a 256 mm cube
 
 // Position of cell (x, y, z), each in [0, 2^LOC_BITS), along the Hilbert curve, in
 // [0, 2^(3 LOC_BITS)). Skilling's transform (J. Skilling, "Programming the Hilbert curve", AIP

@@ -64,7 +64,7 @@ struct GemmAtlas {
     void* bi_bf16 = nullptr;  // [cols_inv_pad][32]
     void* bi_tf32 = nullptr;
     // Columns follow the spatial order of the centroids (Hilbert-curve order of the centre
-    // point's 4 mm cell): spatial position c holds sorted centroid sp_s[c]; directional columns
+    // point's cell): spatial position c holds sorted centroid sp_s[c]; directional columns
     // 2c, 2c+1.
     int* sp_s = nullptr;      // [M]
     float4* cen_sp = nullptr; // [M][21] centroid rows in spatial order, point-major

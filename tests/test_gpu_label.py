@@ -164,7 +164,7 @@ def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
 
 @pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_bf16", "gemm_inv_tf32"])
 def test_gemm_locality_order_extremes(dev, mode):
-    """The GEMM modes visit fibers in the order of their centre point's 4 mm cell. Centres far
+    """The GEMM modes visit fibers in the order of their centre point's 2 mm cell. Centres far
     outside the cell grid (clamped to its border), thousands of fibers in one cell, and a NaN
     centre (sorted to cell 0) still give the plain kernel's results in the caller's order."""
     a = synth.make_atlas(30, per_bundle=20, seed=41)
