@@ -142,14 +142,18 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def traffic_for(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it matches."""
+def traffic_for(kernel: str, mode: str, n: int):
+    """Per-launch DRAM bytes of `kernel` in `mode` from the committed ncu summaries, or None
+    when they were not taken for this kernel instantiation (`kernel@mode`; the plain kernel has
+    one) at this fiber count."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh)
-        return t.get(kernel)
     except (OSError, ValueError):
         return None
+    if t.get("fibers") != n:
+        return None
+    return t.get(f"{kernel}@{mode}", t.get(kernel) if mode == "plain" else None)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -409,7 +413,7 @@ def main():
                 continue
             mr[kname]["kernel"] = KERNEL_NAME[kname]
             mr[kname]["frac"] = mr[kname]["achieved"] / mr[kname]["peak"]
-            mr[kname]["traffic"] = traffic_for(KERNEL_NAME[kname])
+            mr[kname]["traffic"] = traffic_for(KERNEL_NAME[kname], mode, n)
             mr[kname]["ms_per_launch"] = k["ms_per_step"]
             mr[kname]["share_of_step"] = k["ms_per_step"] / r["ms_per_step"]
         roofs[mode] = mr
