@@ -173,7 +173,12 @@ seg_status seg_apply_affine(const float* d_in, int64_t n, const double* h_affine
  *   d_grad_centroids device float32 [M][21][3] or NULL: dC/dc (overwritten, not accumulated).
  *   d_cost          device float64 [1] or NULL: C.
  * The argmax point is recomputed from the fiber and centroid: the lowest point index attaining
- * the maximum point distance in the saved orientation. A zero distance contributes zero.
+ * the maximum point distance in the saved orientation (on FP32 transformed points, as
+ * seg_apply_affine computes them). The residual at that point is recomputed exactly enough
+ * that every per-fiber term is within a few FP32 ulps (error-free FP32 transformations over
+ * the affine split into FP32 high and low parts). The centroid gradient is summed in 64-bit
+ * fixed point (multiples of 2^-36), so it is deterministic and rounded to FP32 once. A zero
+ * distance contributes zero. n may be at most 2^27 fibers per call (SEG_ERR_INVALID_ARG above).
  */
 seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                     const double* h_affine12, const int32_t* d_cidx, const uint8_t* d_orient,
@@ -184,13 +189,15 @@ seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
  * seg_grad without any device allocation, for callers that cannot allocate: code running
  * inside a host allocator callback or a plugin whose host framework owns all device memory,
  * or a process whose device memory is reserved up front. The paper has no counterpart.
- * Arguments, outputs and results are those of seg_grad (the FP64 sums use a different fixed
- * order, so results agree to rounding, not bit for bit). The scratch is a fixed 1.7 MB array
- * inside the library, held by every GPU that loads it until the process exits:
+ * Arguments, outputs and results are those of seg_grad, except that the FP64 sums use a
+ * different fixed order and the centroid gradient is an FP32 atomic sum in no fixed order (so
+ * results agree with seg_grad's to rounding, not bit for bit). The scratch is a fixed 1.7 MB
+ * array inside the library, held by every GPU that loads it until the process exits:
  *  - n may be at most 4,194,304 fibers per call; larger n returns SEG_ERR_INVALID_ARG;
  *  - calls share that array, so calls whose work overlaps on the GPU race: serialize them;
- *  - the first call on each device looks up the array's device address (cudaGetSymbolAddress
- *    with that device current); make that first call before any stream capture.
+ *  - every call looks up the array's device address (cudaGetSymbolAddress, with the caller's
+ *    device current); the first call on a device may load the library's device code there,
+ *    so make that first call before any stream capture.
  * It calls no cudaMalloc, cudaFree or allocating library routine.
  */
 seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64_t n,
@@ -247,6 +254,21 @@ seg_status seg_set_gemm_record_cap(seg_atlas* atlas, int64_t records);
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
                           int64_t* overflow_fibers, int64_t* screened,
                           int64_t* point_distances);
+
+/*
+ * Diagnostic of the tensor-core prune (not in the paper): run the locality sort, the block
+ * culling and the screen of a GEMM mode on n fibers and return the pairs the screen keeps for
+ * the exact test, instead of labels. d_bits is device uint32 [n][words_per_fiber], overwritten:
+ * bit k of fiber f's row is set when the screen keeps column k for f, where k = 2 c + o for
+ * the directional modes (c the caller's centroid index, o = 0 direct, 1 reversed) and k = c for
+ * the orientation-free modes. words_per_fiber >= ceil(2M / 32) (directional) or ceil(M / 32).
+ * Every pair whose float32 exact test passes (d_o^2 <= theta^2) is kept; seg_gemm_stats reports
+ * the screen's counters afterwards (overflow_fibers > 0 means survivors of those fibers were
+ * dropped for lack of record space and the output is incomplete for them).
+ */
+seg_status seg_gemm_screen_bits(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                                seg_mode mode, uint32_t* d_bits, int64_t words_per_fiber,
+                                void* stream);
 
 #ifdef __cplusplus
 }

@@ -50,10 +50,13 @@ def _bind(lib):
                                          ctypes.c_int]
     lib.oracle_near_tie.argtypes = [P, I64, P, P, I64, P, I32, P, P, ctypes.c_double, P,
                                     ctypes.c_int]
+    lib.oracle_near_tie_pruned.argtypes = lib.oracle_near_tie.argtypes
+    lib.oracle_dme_pairs.argtypes = [P, I64, P, I64, P, P, P, P, ctypes.c_int]
     lib.oracle_grad.argtypes = [P, I64, P, P, P, I64, P, I32, P, P, P, P, P, P, P, P, P, P, P,
                                 ctypes.c_int]
     for f in (lib.oracle_dme_matrix, lib.oracle_label_brute, lib.oracle_label_cascade,
-              lib.oracle_near_tie, lib.oracle_grad):
+              lib.oracle_near_tie, lib.oracle_near_tie_pruned, lib.oracle_dme_pairs,
+              lib.oracle_grad):
         f.restype = ctypes.c_int
     return lib
 
@@ -125,9 +128,23 @@ def label(fibers, centroids, bundle_of, thresholds, mode: str = "brute", nthread
     return out
 
 
+def dme_pairs(fibers, centroids, idx, nthreads: int = 0):
+    """(d_ME, direct max, reversed max) of fiber f against centroid idx[f], float64 [n] each
+    (Eq. 1, Eq. 2); NaN where idx[f] < 0."""
+    fib = _f32(fibers).reshape(-1, 63)
+    cen = _f32(centroids).reshape(-1, 63)
+    ix = np.ascontiguousarray(idx, dtype=np.int32)
+    n = fib.shape[0]
+    dme, dd, dr = np.empty(n), np.empty(n), np.empty(n)
+    _check(_load().oracle_dme_pairs(_ptr(fib), n, _ptr(cen), cen.shape[0], _ptr(ix), _ptr(dme),
+                                    _ptr(dd), _ptr(dr), nthreads))
+    return dme, dd, dr
+
+
 def near_tie(fibers, centroids, bundle_of, thresholds, labels, dist, tol: float = 2e-3,
-             nthreads: int = 0):
-    """uint8 [n]: 1 where the label is not decidable at tolerance tol (mm)."""
+             nthreads: int = 0, pruned: bool = False):
+    """uint8 [n]: 1 where the label is not decidable at tolerance tol (mm). pruned=True skips
+    the centroids farther than their threshold + tol (same flags, far less work)."""
     fib = _f32(fibers).reshape(-1, 63)
     cen = _f32(centroids).reshape(-1, 63)
     bo = np.ascontiguousarray(bundle_of, dtype=np.int32)
@@ -136,9 +153,9 @@ def near_tie(fibers, centroids, bundle_of, thresholds, labels, dist, tol: float 
     dist = np.ascontiguousarray(dist, dtype=np.float64)
     n = fib.shape[0]
     flag = np.empty(n, np.uint8)
-    _check(_load().oracle_near_tie(_ptr(fib), n, _ptr(cen), _ptr(bo), cen.shape[0], _ptr(thr),
-                                   thr.shape[0], _ptr(lab), _ptr(dist), tol, _ptr(flag),
-                                   nthreads))
+    fn = _load().oracle_near_tie_pruned if pruned else _load().oracle_near_tie
+    _check(fn(_ptr(fib), n, _ptr(cen), _ptr(bo), cen.shape[0], _ptr(thr), thr.shape[0],
+              _ptr(lab), _ptr(dist), tol, _ptr(flag), nthreads))
     return flag
 
 

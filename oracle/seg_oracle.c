@@ -389,6 +389,82 @@ int oracle_near_tie(const float *fib, int64_t n, const float *cen, const int32_t
     return 0;
 }
 
+/* The same flags as oracle_near_tie, with centroids that cannot matter skipped. Both conditions
+ * need d(f,c) <= theta_b(c) + tol, and each orientation's running maximum of point distances is
+ * a lower bound of its full maximum, so a centroid is skipped as soon as both running maxima
+ * exceed theta + tol (centre point first, then the end points, then the rest, as in the
+ * progressive discarding of Section 2.3). Every centroid that is not skipped gets the full
+ * d_ME of Eq. 2, and the flag is decided exactly as in oracle_near_tie. */
+int oracle_near_tie_pruned(const float *fib, int64_t n, const float *cen,
+                           const int32_t *bundle_of, int64_t M, const float *thr, int32_t B,
+                           const int32_t *labels, const double *dist, double tol,
+                           uint8_t *flag, int nthreads) {
+    double *C = malloc((size_t)(M > 0 ? M : 1) * NC * sizeof(double));
+    if (!C) return 1;
+    promote(cen, C, M * NC);
+    (void)B;
+    /* point visiting order: centre, ends, the test3 points, then the rest */
+    int order[NPTS];
+    int k = 0;
+    order[k++] = CENTRE;
+    order[k++] = 0;
+    order[k++] = NPTS - 1;
+    for (int q = 0; q < 4; ++q) order[k++] = TEST3[q];
+    for (int i = 1; i < NPTS - 1; ++i)
+        if (i != CENTRE && i != 5 && i != 15 && i != 3 && i != 17) order[k++] = i;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t f = 0; f < n; ++f) {
+        double a[NC];
+        promote(fib + f * NC, a, NC);
+        uint8_t fl = 0;
+        if (all_finite(a)) {
+            double D = dist[f];
+            for (int64_t c = 0; c < M && !fl; ++c) {
+                const double *b = C + c * NC;
+                double th = (double)thr[bundle_of[c]];
+                double lim = th + tol;
+                double md = 0.0, mr = 0.0;
+                for (int q = 0; q < NPTS && (md <= lim || mr <= lim); ++q) {
+                    int i = order[q];
+                    double e = d_E(a + 3 * i, b + 3 * i);
+                    double g = d_E(a + 3 * i, b + 3 * rev(i));
+                    if (e > md) md = e;
+                    if (g > mr) mr = g;
+                }
+                if (md > lim && mr > lim) continue; /* d > theta + tol: neither condition */
+                double d = md <= mr ? md : mr;
+                if ((labels[f] < 0 || d <= D + tol) && fabs(d - th) <= tol) fl = 1;
+                if (bundle_of[c] != labels[f] && d <= th + tol && fabs(d - D) <= tol) fl = 1;
+            }
+        }
+        flag[f] = fl;
+    }
+    free(C);
+    return 0;
+}
+
+/* d_ME and both orientation maxima of fiber f against centroid idx[f] (Eq. 1, Eq. 2): one pair
+ * per fiber; idx[f] < 0 gives NaN. */
+int oracle_dme_pairs(const float *fib, int64_t n, const float *cen, int64_t M,
+                     const int32_t *idx, double *dme, double *dd, double *dr, int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t f = 0; f < n; ++f) {
+        double x = NAN, y = NAN;
+        if (idx[f] >= 0 && idx[f] < M) {
+            double a[NC], b[NC];
+            promote(fib + f * NC, a, NC);
+            promote(cen + (int64_t)idx[f] * NC, b, NC);
+            dme_both(a, b, &x, &y);
+        }
+        if (dd) dd[f] = x;
+        if (dr) dr[f] = y;
+        if (dme) dme[f] = x < y ? x : y;
+    }
+    return 0;
+}
+
 /* y = M x + t for every point, in double. aff = M row-major (9) then t (3). */
 static void apply_affine(const double *aff, const double *x, double *y) {
     for (int p = 0; p < NPTS; ++p) {

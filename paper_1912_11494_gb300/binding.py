@@ -44,6 +44,7 @@ SIGNATURES = [
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    ("seg_gemm_screen_bits", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P]),
     ("seg_profile_enable", ctypes.c_int, [_P, _I32]),
     ("seg_profile_read", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64),
                                         ctypes.POINTER(ctypes.c_double)]),
@@ -238,6 +239,19 @@ def seg_grad_noalloc(atlas: Atlas, fibers, affine12, cidx, orient, grad_affine,
                                   ctypes.cast(buf, ctypes.c_void_p), _ptr(cidx), _ptr(orient),
                                   _ptr(grad_affine), _ptr(grad_centroids), _ptr(cost),
                                   _stream(stream)))
+
+
+def seg_gemm_screen_bits(atlas: Atlas, fibers, mode, stream=None):
+    """Pairs the tensor-core screen of a GEMM mode keeps, as uint32 [n, words] bit rows (bit
+    2c+o for directional modes, c for orientation-free ones, caller's centroid numbering)."""
+    fib = _dev(fibers, torch.float32, "fibers").contiguous()
+    m = _mode(mode)
+    cols = atlas.M if m in (MODES["gemm_inv_bf16"], MODES["gemm_inv_tf32"]) else 2 * atlas.M
+    words = (cols + 31) // 32
+    bits = torch.empty((fib.shape[0], words), dtype=torch.int32, device=fib.device)
+    _check(lib().seg_gemm_screen_bits(atlas.handle, _ptr(fib), int(fib.shape[0]), m,
+                                      _ptr(bits), words, _stream(stream)))
+    return bits
 
 
 def seg_sync_status(atlas: Atlas, stream=None):

@@ -1233,6 +1233,40 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __rest
     if (orient) orient[o] = (unsigned char)(k & 1ull);
 }
 
+// Diagnostic output of the screen (seg_gemm_screen_bits): every surviving (fiber, column) of the
+// block records as one bit per (caller fiber, caller centroid [, orientation]); one warp per
+// record, lanes over its 32 fibers.
+__global__ void k_survivor_bits(long long n, AtlasView at, GemmScratch g, int inv,
+                                unsigned* __restrict__ bits, long long words,
+                                long long pairs, long long* __restrict__ stats) {
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w0 == 0 && lane == 0 && stats) {
+        stats[0] = pairs;
+        stats[1] = (long long)g.cnt[2];
+        stats[2] = (long long)g.cnt[1];
+        stats[3] = (long long)g.cnt[3];
+        stats[4] = 0;
+    }
+    const long long cnt = min((long long)g.cnt[0], g.cap);
+    for (long long b = w0; b < cnt; b += nw) {
+        const uint2 h = g.hdr[b];
+        if (h.x == EMPTY_SLOT) continue;
+        const long long f = (long long)h.x + lane;
+        unsigned m = g.mask[b * 32 + lane];
+        if (f >= n) continue;
+        const long long fo = g.perm[f];
+        for (; m; m &= m - 1) {
+            const unsigned col = h.y + (unsigned)(__ffs(m) - 1);
+            const int sp = inv ? (int)col : (int)(col >> 1);
+            const long long c = at.perm[g.sp_s[sp]];
+            const long long bit = inv ? c : 2 * c + (col & 1u);
+            atomicOr(bits + fo * words + (bit >> 5), 1u << (bit & 31));
+        }
+    }
+}
+
 // ---- host side ---------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1374,7 +1408,7 @@ void free_gemm_atlas(GemmAtlas* g) {
 seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, std::mutex* mu,
                       const float* fib, long long n, int mode, int* labels, float* dist,
                       int* cidx, unsigned char* orient, cudaStream_t st, int config,
-                      Profiler* prof) {
+                      Profiler* prof, unsigned* dbg_bits, long long dbg_words) {
     const bool tf32 = mode == SEG_MODE_GEMM_TF32 || mode == SEG_MODE_GEMM_INV_TF32;
     const bool inv = mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
     const int fmt = tf32 ? 2 : 1;
@@ -1490,6 +1524,16 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_SCREEN, st);
         e = dispatch_screen(sh, ta, tb, n_units, n_tiles, cols, g, at.status, sms, st);
+    }
+    if (!e && dbg_bits) {  // diagnostic: the screen's survivors instead of labels
+        e = cudaMemsetAsync(dbg_bits, 0, (size_t)n * dbg_words * 4, st);
+        if (!e)
+            k_survivor_bits<<<sms * 8, 256, 0, st>>>(n, at, g, inv ? 1 : 0, dbg_bits, dbg_words,
+                                                     n * (long long)cols, ga->stats);
+        if (!e) e = cudaGetLastError();
+        seg_status r = scratch_release(scratch, st);
+        if (e) return cuda_fail(e, "seg_gemm_screen_bits");
+        return r;
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);

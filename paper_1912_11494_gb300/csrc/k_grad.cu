@@ -1,35 +1,28 @@
 // Affine transform of fibers and the adjoint of the segmentation cost (not in the paper).
 //
-// C(T) = sum over labelled fibers f of d_ME(T f, c_sigma(f)), T f = A f + t on every point. With
-// the structure (centroid sigma, orientation o, argmax point i*) fixed, d_ME = |r| with
-// r = T(a_i*) - c_pi(i*), pi(i) = i or 20 - i (Eq. 2), so
-//   dC/dA_rc += u_r a_i*,c,  dC/dt_r += u_r,  dC/dc_pi(i*),r -= u_r,  u = r / |r|.
-// Per-fiber terms are FP32. The sum over fibers of the 13 affine/cost terms is FP64 with a fixed
-// assignment of fibers to threads and a fixed tree, so it is deterministic; the centroid gradient
-// is an FP32 scatter-add.
+// C(T) = sum over labelled fibers f of d_ME(T f, c_sigma(f)); the per-fiber terms (argmax point,
+// residual, unit vector) are computed in FP32 by fiber_grad (seg_grad_terms.cuh), with the
+// residual recovered by error-free transformations. The sum over fibers of the 13 affine/cost
+// terms is FP64 with a fixed assignment of fibers to threads and a fixed tree, so it is
+// deterministic. The centroid gradient is summed exactly: each term -u_r is rounded to a
+// multiple of 2^-36 and added as a 64-bit integer (integer addition is exact and does not depend
+// on the order), then each coordinate is converted to FP32 once; so the centroid gradient is
+// deterministic and within half an FP32 ulp plus count x 2^-37 of the sum of the FP32 terms.
+#include <algorithm>
+
 #include "seg_internal.cuh"
-#include "seg_exact.cuh"
+#include "seg_grad_terms.cuh"
 
 namespace seg {
 namespace {
 
-struct Affine {
-    float m[12];  // A row-major, then t
-};
-
-__device__ __forceinline__ void affine_point(const Affine& T, const float* x, float* y) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-        y[r] = fmaf(T.m[3 * r], x[0], fmaf(T.m[3 * r + 1], x[1], fmaf(T.m[3 * r + 2], x[2], T.m[9 + r])));
-}
-
-__global__ void k_apply_affine(const float* __restrict__ in, long long npoints, Affine T,
+__global__ void k_apply_affine(const float* __restrict__ in, long long npoints, AffineDS T,
                                float* __restrict__ out) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npoints;
          p += (long long)gridDim.x * blockDim.x) {
         float x[3] = {in[3 * p], in[3 * p + 1], in[3 * p + 2]};
         float y[3];
-        affine_point(T, x, y);
+        affine_point_hi(T, x, y);
         out[3 * p] = y[0];
         out[3 * p + 1] = y[1];
         out[3 * p + 2] = y[2];
@@ -38,11 +31,14 @@ __global__ void k_apply_affine(const float* __restrict__ in, long long npoints, 
 
 constexpr int GRAD_THREADS = 256;
 constexpr int GRAD_BLOCKS = 1024;  // fixed, so the FP64 summation order never changes
+constexpr float CEN_SCALE = 68719476736.0f;  // 2^36: fixed point of the centroid gradient
+// |term| <= 1, so 2^27 contributions to one coordinate stay below 2^63
+constexpr long long GRAD_MAX_FIBERS = 1LL << 27;
 
 __global__ void __launch_bounds__(GRAD_THREADS)
-k_grad(const float* __restrict__ fib, long long n, Affine T, const int* __restrict__ cidx,
+k_grad(const float* __restrict__ fib, long long n, AffineDS T, const int* __restrict__ cidx,
        const unsigned char* __restrict__ orient, AtlasView at, const int* __restrict__ inv_perm,
-       float* __restrict__ grad_cen, double* __restrict__ partial) {
+       unsigned long long* __restrict__ gcen_fx, double* __restrict__ partial) {
     double acc[13];
 #pragma unroll
     for (int k = 0; k < 13; ++k) acc[k] = 0.0;
@@ -50,36 +46,18 @@ k_grad(const float* __restrict__ fib, long long n, Affine T, const int* __restri
          f += (long long)GRAD_BLOCKS * GRAD_THREADS) {
         const int c = cidx[f];
         if (c < 0 || c >= at.M) continue;
-        const int o = orient[f] ? 1 : 0;
-        const float* x = fib + f * NC;
         const float* b = at.cen + (size_t)inv_perm[c] * CROW;
-        float y[NC];
+        const FiberGrad g = fiber_grad(T, fib + f * NC, b, orient[f] ? 1 : 0);
+        acc[12] += (double)g.d;
+        if (!g.valid) continue;
 #pragma unroll
-        for (int p = 0; p < NPTS; ++p) affine_point(T, x + 3 * p, y + 3 * p);
-        float best = -1.0f;
-        int is = 0;
+        for (int r = 0; r < 3; ++r) {
 #pragma unroll
-        for (int i = 0; i < NPTS; ++i) {
-            const float d2 = pd2(y, i, b, o ? NPTS - 1 - i : i);
-            if (d2 > best) {
-                best = d2;
-                is = i;
-            }
-        }
-        const int j = o ? NPTS - 1 - is : is;
-        const float r0 = y[3 * is] - b[3 * j], r1 = y[3 * is + 1] - b[3 * j + 1],
-                    r2 = y[3 * is + 2] - b[3 * j + 2];
-        const float d = sqrtf(best);
-        acc[12] += (double)d;
-        if (d > 0.0f) {
-            const float u[3] = {r0 / d, r1 / d, r2 / d};
-            const float xs[3] = {x[3 * is], x[3 * is + 1], x[3 * is + 2]};
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) acc[3 * r + q] += (double)(u[r] * xs[q]);
-                acc[9 + r] += (double)u[r];
-                if (grad_cen) atomicAdd(grad_cen + ((size_t)c * NPTS + j) * 3 + r, -u[r]);
+            for (int q = 0; q < 3; ++q) acc[3 * r + q] += (double)(g.u[r] * g.x[q]);
+            acc[9 + r] += (double)g.u[r];
+            if (gcen_fx) {
+                const long long v = __float2ll_rn(-g.u[r] * CEN_SCALE);
+                atomicAdd(gcen_fx + ((size_t)c * NPTS + g.j) * 3 + r, (unsigned long long)v);
             }
         }
     }
@@ -117,12 +95,12 @@ __global__ void k_grad_final(const double* __restrict__ partial, double* __restr
     }
 }
 
-bool load_affine(const double* h, Affine* T) {
-    for (int k = 0; k < 12; ++k) {
-        if (!std::isfinite(h[k])) return false;
-        T->m[k] = (float)h[k];
-    }
-    return true;
+// Fixed point -> FP32: the integer is rounded to FP32 once, then scaled by 2^-36 (exact).
+__global__ void k_grad_cen_out(const unsigned long long* __restrict__ gcen_fx, long long count,
+                               float* __restrict__ grad_cen) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        grad_cen[i] = __ll2float_rn((long long)gcen_fx[i]) * (1.0f / CEN_SCALE);
 }
 
 }  // namespace
@@ -131,22 +109,35 @@ seg_status grad_launch(const AtlasView& at, const int* inv_perm, ScratchArena* s
                        std::mutex* mu, const float* fib, long long n, const double* h_aff,
                        const int* cidx, const unsigned char* orient, double* grad_aff,
                        float* grad_cen, double* cost, cudaStream_t st) {
-    Affine T;
-    if (!load_affine(h_aff, &T)) return fail(SEG_ERR_INVALID_ARG, "seg_grad: non-finite affine");
+    AffineDS T;
+    if (!split_affine(h_aff, &T)) return fail(SEG_ERR_INVALID_ARG, "seg_grad: non-finite affine");
+    if (n > GRAD_MAX_FIBERS)
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad: n=%lld exceeds %lld fibers per call", n,
+                    GRAD_MAX_FIBERS);
+    const size_t part_bytes = sizeof(double) * GRAD_BLOCKS * 13;
+    const long long ncoord = (long long)at.M * NC;
+    const size_t bytes = part_bytes + (grad_cen ? sizeof(unsigned long long) * ncoord : 0);
     std::lock_guard<std::mutex> lock(*mu);
     void* buf = nullptr;
-    seg_status s = scratch_acquire(scratch, sizeof(double) * GRAD_BLOCKS * 13, st, &buf);
+    seg_status s = scratch_acquire(scratch, bytes, st, &buf);
     if (s != SEG_OK) return s;
+    unsigned long long* gfx =
+        grad_cen ? reinterpret_cast<unsigned long long*>(static_cast<char*>(buf) + part_bytes)
+                 : nullptr;
     cudaError_t e = cudaSuccess;
-    if (grad_cen)
-        e = cudaMemsetAsync(grad_cen, 0, sizeof(float) * (size_t)at.M * NC, st);
+    if (gfx) e = cudaMemsetAsync(gfx, 0, sizeof(unsigned long long) * ncoord, st);
     if (!e) {
-        k_grad<<<GRAD_BLOCKS, GRAD_THREADS, 0, st>>>(fib, n, T, cidx, orient, at, inv_perm,
-                                                     grad_cen, (double*)buf);
+        k_grad<<<GRAD_BLOCKS, GRAD_THREADS, 0, st>>>(fib, n, T, cidx, orient, at, inv_perm, gfx,
+                                                     (double*)buf);
         e = cudaGetLastError();
     }
     if (!e) {
         k_grad_final<<<1, 13 * 32, 0, st>>>((const double*)buf, grad_aff, cost);
+        e = cudaGetLastError();
+    }
+    if (!e && gfx) {
+        const long long blocks = std::min<long long>((ncoord + 255) / 256, 152 * 8);
+        k_grad_cen_out<<<(unsigned)blocks, 256, 0, st>>>(gfx, ncoord, grad_cen);
         e = cudaGetLastError();
     }
     seg_status r = scratch_release(scratch, st);
@@ -156,8 +147,8 @@ seg_status grad_launch(const AtlasView& at, const int* inv_perm, ScratchArena* s
 
 seg_status apply_affine_launch(const float* in, long long n, const double* h_aff, float* out,
                                cudaStream_t st) {
-    Affine T;
-    if (!load_affine(h_aff, &T))
+    AffineDS T;
+    if (!split_affine(h_aff, &T))
         return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: non-finite affine");
     const long long np = n * NPTS;
     long long blocks = (np + 255) / 256;

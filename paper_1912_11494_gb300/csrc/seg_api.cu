@@ -515,6 +515,32 @@ seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64
                                (cudaStream_t)stream);
 }
 
+seg_status seg_gemm_screen_bits(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                                seg_mode mode, uint32_t* d_bits, int64_t words_per_fiber,
+                                void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: n < 0");
+    if ((int)mode < SEG_MODE_GEMM_BF16 || (int)mode > SEG_MODE_GEMM_INV_TF32)
+        return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: mode %d is not a GEMM mode",
+                    (int)mode);
+    const bool inv = mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
+    const int64_t need = ((inv ? 1 : 2) * (int64_t)atlas->view.M + 31) / 32;
+    if (words_per_fiber < need)
+        return fail(SEG_ERR_INVALID_ARG,
+                    "seg_gemm_screen_bits: words_per_fiber=%lld < %lld", (long long)words_per_fiber,
+                    (long long)need);
+    if (n > 0 && (!d_fibers || !d_bits))
+        return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: NULL fibers or bits");
+    if (unaligned4(d_fibers) || unaligned4(d_bits))
+        return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: a buffer is not 4-byte aligned");
+    if (n == 0) return SEG_OK;
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    return label_gemm(a->view, &a->gemm, &a->scratch, &a->mu, d_fibers, n, (int)mode, nullptr,
+                      nullptr, nullptr, nullptr, (cudaStream_t)stream, a->config[(int)mode],
+                      nullptr, d_bits, words_per_fiber);
+}
+
 seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable) {
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_profile_enable: atlas is NULL");

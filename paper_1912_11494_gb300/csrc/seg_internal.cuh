@@ -81,7 +81,8 @@ int gemm_num_configs();
 seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,
                       const float* fib, long long n, int mode, int* labels, float* dist,
                       int* cidx, unsigned char* orient, cudaStream_t st, int config,
-                      Profiler* prof = nullptr);
+                      Profiler* prof = nullptr, unsigned* dbg_bits = nullptr,
+                      long long dbg_words = 0);
 
 // Cached CUDA graph of the batched launch: counter reset, work-table upload (from a pinned
 // host copy the host rewrites before each replay) and the persistent kernel.

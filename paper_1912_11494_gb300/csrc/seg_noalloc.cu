@@ -13,13 +13,12 @@
 // whose work overlaps on the GPU race on it (serialize them, e.g. on one stream). Every call
 // writes every slot it later reads, so nothing needs clearing between calls.
 //
-// In host code the array's name is only a host-side stand-in, not a device address. The first
-// call on each device looks up the array's device address with cudaGetSymbolAddress while that
-// device is current and caches it; make that first call before any stream capture.
-#include <mutex>
-
+// In host code the array's name is only a host-side stand-in, not a device address. Every call
+// looks up the array's device address with cudaGetSymbolAddress while the caller's device is
+// current (the first call on a device may load the module there; make that first call before
+// any stream capture).
 #include "seg_internal.cuh"
-#include "seg_exact.cuh"
+#include "seg_grad_terms.cuh"
 
 namespace seg {
 namespace {
@@ -27,27 +26,14 @@ namespace {
 constexpr int NA_THREADS = 256;
 constexpr long long NA_MAX_BLOCKS = 16384;
 constexpr long long NA_MAX_FIBERS = NA_MAX_BLOCKS * NA_THREADS;  // 4,194,304
-constexpr int NA_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double g_na_partials[NA_MAX_BLOCKS * 13];
 
-std::mutex g_na_mu;
-double* g_na_ptr[NA_MAX_DEVICES] = {};
-
-struct NaAffine {
-    float m[12];
-};
-
-__device__ __forceinline__ void na_affine_point(const NaAffine& T, const float* x, float* y) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-        y[r] = fmaf(T.m[3 * r], x[0], fmaf(T.m[3 * r + 1], x[1], fmaf(T.m[3 * r + 2], x[2], T.m[9 + r])));
-}
-
-// One thread per fiber: the same per-fiber terms as seg_grad (argmax point of the saved
-// orientation, u = r / |r|), summed per block in FP64 into partial[blockIdx.x].
+// One thread per fiber: the per-fiber terms of seg_grad (fiber_grad), summed per block in FP64
+// into partial[blockIdx.x]; the centroid gradient is an FP32 atomic sum (seg_grad sums it in
+// fixed point, which needs scratch sized by the atlas).
 __global__ void __launch_bounds__(NA_THREADS)
-k_grad_na(const float* __restrict__ fib, long long n, NaAffine T, const int* __restrict__ cidx,
+k_grad_na(const float* __restrict__ fib, long long n, AffineDS T, const int* __restrict__ cidx,
           const unsigned char* __restrict__ orient, AtlasView at, const int* __restrict__ inv_perm,
           float* __restrict__ grad_cen, double* __restrict__ partial) {
     double acc[13];
@@ -57,36 +43,17 @@ k_grad_na(const float* __restrict__ fib, long long n, NaAffine T, const int* __r
     if (f < n) {
         const int c = cidx[f];
         if (c >= 0 && c < at.M) {
-            const int o = orient[f] ? 1 : 0;
-            const float* x = fib + f * NC;
             const float* b = at.cen + (size_t)inv_perm[c] * CROW;
-            float y[NC];
-#pragma unroll
-            for (int p = 0; p < NPTS; ++p) na_affine_point(T, x + 3 * p, y + 3 * p);
-            float best = -1.0f;
-            int is = 0;
-#pragma unroll
-            for (int i = 0; i < NPTS; ++i) {
-                const float d2 = pd2(y, i, b, o ? NPTS - 1 - i : i);
-                if (d2 > best) {
-                    best = d2;
-                    is = i;
-                }
-            }
-            const int j = o ? NPTS - 1 - is : is;
-            const float r0 = y[3 * is] - b[3 * j], r1 = y[3 * is + 1] - b[3 * j + 1],
-                        r2 = y[3 * is + 2] - b[3 * j + 2];
-            const float d = sqrtf(best);
-            acc[12] = (double)d;
-            if (d > 0.0f) {
-                const float u[3] = {r0 / d, r1 / d, r2 / d};
-                const float xs[3] = {x[3 * is], x[3 * is + 1], x[3 * is + 2]};
+            const FiberGrad g = fiber_grad(T, fib + f * NC, b, orient[f] ? 1 : 0);
+            acc[12] = (double)g.d;
+            if (g.valid) {
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) acc[3 * r + q] = (double)(u[r] * xs[q]);
-                    acc[9 + r] = (double)u[r];
-                    if (grad_cen) atomicAdd(grad_cen + ((size_t)c * NPTS + j) * 3 + r, -u[r]);
+                    for (int q = 0; q < 3; ++q) acc[3 * r + q] = (double)(g.u[r] * g.x[q]);
+                    acc[9 + r] = (double)g.u[r];
+                    if (grad_cen)
+                        atomicAdd(grad_cen + ((size_t)c * NPTS + g.j) * 3 + r, -g.u[r]);
                 }
             }
         }
@@ -125,24 +92,16 @@ __global__ void k_grad_na_final(const double* __restrict__ partial, int nb,
     }
 }
 
-// Device address of g_na_partials for the current device, looked up once per device.
+// Device address of g_na_partials in the current device's copy of the module. Looked up on
+// every call (cheap once the module is loaded), so a device reset that reloads the module at
+// another address is harmless.
 seg_status na_scratch(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e) return cuda_fail(e, "seg_grad_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= NA_MAX_DEVICES)
-        return fail(SEG_ERR_UNSUPPORTED, "seg_grad_noalloc: device ordinal %d >= %d", dev,
-                    NA_MAX_DEVICES);
-    std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_ptr[dev]) {
-        double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, g_na_partials);
-        if (e != cudaSuccess || !p)
-            return cuda_fail(e ? e : cudaErrorInvalidSymbol,
-                             "seg_grad_noalloc: cudaGetSymbolAddress of the static scratch");
-        g_na_ptr[dev] = p;
-    }
-    *out = g_na_ptr[dev];
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_na_partials);
+    if (e != cudaSuccess || !p)
+        return cuda_fail(e ? e : cudaErrorInvalidSymbol,
+                         "seg_grad_noalloc: cudaGetSymbolAddress of the static scratch");
+    *out = p;
     return SEG_OK;
 }
 
@@ -157,12 +116,9 @@ seg_status grad_noalloc_launch(const AtlasView& at, const int* inv_perm, const f
                     "seg_grad_noalloc: n=%lld exceeds the static scratch limit of %lld fibers "
                     "per call",
                     (long long)n, (long long)NA_MAX_FIBERS);
-    NaAffine T;
-    for (int k = 0; k < 12; ++k) {
-        if (!std::isfinite(h_aff[k]))
-            return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: non-finite affine");
-        T.m[k] = (float)h_aff[k];
-    }
+    AffineDS T;
+    if (!split_affine(h_aff, &T))
+        return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: non-finite affine");
     double* partial = nullptr;
     seg_status s = na_scratch(&partial);
     if (s != SEG_OK) return s;

@@ -47,3 +47,47 @@ def compare(fib, cen, bundle_of, thr, labels, dist, cidx=None, orient=None, nthr
                 assert np.abs(od - dist[lab]).max() <= DIST_TOL
     return dict(near_ties=int(flag.sum()), n=len(fib), labelled=int((labels >= 0).sum()),
                 ref=ref, flag=flag)
+
+
+def compare_all(fib, cen, bundle_of, thr, labels, dist, cidx=None, orient=None, ref=None,
+                count_ties: bool = True, nthreads=0):
+    """Every fiber against the oracle's cascade (identical to the brute definition, pinned on
+    the CPU), at sizes where the brute near-tie scan over all fibers would be too slow: the
+    near-tie flag is computed exactly (oracle.near_tie, pruned) for the fibers whose labels
+    differ, which must all be near-ties, and, if count_ties, for all fibers to report how many
+    are not decidable. ref: a precomputed oracle.label(..., "cascade") result."""
+    fib = np.ascontiguousarray(fib, np.float32)
+    if ref is None:
+        ref = oracle.label(fib, cen, bundle_of, thr, "cascade", nthreads=nthreads)
+    labels = np.asarray(labels)
+    dist = np.asarray(dist, np.float64)
+    diff = np.nonzero(labels != ref["labels"])[0]
+    if diff.size:
+        fl = oracle.near_tie(fib[diff], cen, bundle_of, thr, ref["labels"][diff],
+                             ref["dist"][diff], TIE_TOL, nthreads=nthreads, pruned=True)
+        bad = diff[fl == 0]
+        assert bad.size == 0, (f"{bad.size} decidable label mismatches, first {bad[:5]}: gpu "
+                               f"{labels[bad[:5]]} oracle {ref['labels'][bad[:5]]}")
+    both = (labels >= 0) & (ref["labels"] >= 0)
+    if both.any():
+        err = np.abs(dist[both] - ref["dist"][both])
+        assert err.max() <= DIST_TOL, f"max distance error {err.max()}"
+    fin = np.isfinite(fib.reshape(len(fib), -1)).all(axis=1)
+    assert np.all(np.isinf(dist[(labels < 0) & fin]))
+    assert np.all(np.isnan(dist[~fin])) and np.all(labels[~fin] == -1)
+    if cidx is not None:
+        cidx = np.asarray(cidx)
+        assert np.all((cidx >= 0) == (labels >= 0))
+        lab = np.nonzero(labels >= 0)[0]
+        assert np.all(np.asarray(bundle_of)[cidx[lab]] == labels[lab])
+        own, dd, dr = oracle.dme_pairs(fib[lab], cen, cidx[lab], nthreads=nthreads)
+        assert np.abs(own - dist[lab]).max() <= DIST_TOL
+        if orient is not None:
+            o = np.asarray(orient)[lab]
+            assert np.abs(np.where(o == 0, dd, dr) - dist[lab]).max() <= DIST_TOL
+    ties = None
+    if count_ties:
+        ties = int(oracle.near_tie(fib, cen, bundle_of, thr, ref["labels"], ref["dist"],
+                                   TIE_TOL, nthreads=nthreads, pruned=True).sum())
+    return dict(n=len(fib), labelled=int((labels >= 0).sum()), mismatches=int(diff.size),
+                near_ties=ties, ref=ref)

@@ -262,6 +262,52 @@ def test_near_tie_flags():
     assert list(oracle.near_tie(fib, cen, bo, thr2, r2["labels"], r2["dist"])) == [1, 0, 1]
 
 
+def test_near_tie_pruned_equals_brute(small_workload):
+    """The pruned near-tie scan skips only centroids farther than theta + tol, which neither
+    condition can use: its flags equal the full scan's on the hand-built cases above and on the
+    whole 10,000-fiber x 1,000-centroid workload, at the parity tolerance and at a tolerance so
+    wide that many fibers are flagged."""
+    t = np.arange(21, dtype=np.float32)
+    base = np.stack([t, 0 * t, 0 * t], axis=1)
+    cen = np.stack([base + np.array(o, np.float32) for o in [(0, 0, 3), (0, 3.001, 0),
+                                                               (0, 0, 20)]])
+    bo = np.array([0, 1, 2], np.int32)
+    fib = np.stack([base, base + np.array([0, 0, 18.0], np.float32),
+                    base + np.array([0, 0, 8.0], np.float32)])
+    for thr in (np.array([5.0, 5.0, 5.0], np.float32), np.array([5.0, 5.0, 2.5], np.float32)):
+        r = oracle.label(fib, cen, bo, thr)
+        a = oracle.near_tie(fib, cen, bo, thr, r["labels"], r["dist"])
+        b = oracle.near_tie(fib, cen, bo, thr, r["labels"], r["dist"], pruned=True)
+        assert list(a) == list(b)
+    atlas, f = small_workload
+    r = oracle.label(f, atlas.centroids, atlas.bundle_of, atlas.thresholds, "cascade")
+    for tol in (2e-3, 1.0):
+        a = oracle.near_tie(f, atlas.centroids, atlas.bundle_of, atlas.thresholds, r["labels"],
+                            r["dist"], tol)
+        b = oracle.near_tie(f, atlas.centroids, atlas.bundle_of, atlas.thresholds, r["labels"],
+                            r["dist"], tol, pruned=True)
+        np.testing.assert_array_equal(a, b)
+        if tol > 0.1:
+            assert a.sum() > 40
+
+
+def test_dme_pairs_equals_matrix_diagonal():
+    """One pair per fiber gives the diagonal of the full d_ME matrix; a negative index gives
+    NaN."""
+    rng = np.random.default_rng(5)
+    fib = _rand_fibers(rng, 40)
+    cen = _rand_fibers(rng, 40)
+    d, dd, dr = oracle.dme_matrix(fib, cen)
+    idx = np.arange(40, dtype=np.int32)
+    p, pd, pr = oracle.dme_pairs(fib, cen, idx)
+    np.testing.assert_array_equal(p, np.diagonal(d))
+    np.testing.assert_array_equal(pd, np.diagonal(dd))
+    np.testing.assert_array_equal(pr, np.diagonal(dr))
+    idx[3] = -1
+    p, _, _ = oracle.dme_pairs(fib, cen, idx)
+    assert np.isnan(p[3]) and np.isfinite(np.delete(p, 3)).all()
+
+
 def test_grad_translation_closed_form():
     """One fiber, one centroid, translation only: dC/dt = u = r/|r| at the argmax point."""
     t = np.arange(21, dtype=np.float32)

@@ -4,7 +4,9 @@ Some callers cannot allocate device memory: code inside a host allocator callbac
 whose host framework owns every device allocation, or a process that reserved all device memory
 up front. seg_grad may grow a scratch buffer with cudaMalloc; seg_grad_noalloc uses a fixed
 array compiled into the library instead. This test calls it through the C ABI twice in a row
-and checks each result against seg_grad's, and checks that an oversized call is refused.
+on an atlas whose scratch has never been grown, checks that the device's free memory does not
+change across those calls, checks each result against seg_grad's, and checks that an oversized
+call is refused.
 
 This file is named so that pytest collects it last.
 """
@@ -21,6 +23,8 @@ MAX_FIBERS = 4_194_304
 
 @pytest.fixture(scope="module")
 def setup():
+    """A freshly created atlas on which seg_grad has never run, so its scratch arena is still
+    empty, and the forward pass's structure for 5,000 transformed fibers."""
     assert torch.cuda.is_available()
     from paper_1912_11494_gb300 import build
     build.build()
@@ -41,30 +45,39 @@ def setup():
     return dev, a, at, fib, aff, cidx, orient
 
 
-def grads(fn, setup):
+def outputs(setup):
+    dev, a = setup[0], setup[1]
+    return (torch.full((12,), np.nan, dtype=torch.float64, device=dev),
+            torch.full((a.M, 21, 3), np.nan, dtype=torch.float32, device=dev),
+            torch.full((1,), np.nan, dtype=torch.float64, device=dev))
+
+
+def run(fn, setup, out):
     dev, a, at, fib, aff, cidx, orient = setup
-    ga = torch.full((12,), np.nan, dtype=torch.float64, device=dev)
-    gc = torch.full((a.M, 21, 3), np.nan, dtype=torch.float32, device=dev)
-    cost = torch.full((1,), np.nan, dtype=torch.float64, device=dev)
+    ga, gc, cost = out
     fn(at, fib, aff, cidx, orient, ga, gc, cost)
     binding.seg_sync_status(at)
     return ga.cpu().numpy(), gc.cpu().numpy(), float(cost.item())
 
 
 def test_noalloc_matches_seg_grad_twice(setup):
-    ref_a, ref_c, ref_cost = grads(binding.seg_grad, setup)
+    # the allocation-free calls come first on this atlas: nothing may have grown its scratch
+    outs = [outputs(setup) for _ in range(3)]
+    run(binding.seg_grad_noalloc, setup, outs[0])      # first call on the device: module load
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    got = [run(binding.seg_grad_noalloc, setup, outs[k]) for k in (1, 2)]
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0, "seg_grad_noalloc allocated device memory"
+    ref_a, ref_c, ref_cost = run(binding.seg_grad, setup, outputs(setup))
     assert ref_cost > 0 and np.isfinite(ref_a).all()
-    prev = None
-    for _ in range(2):
-        ga, gc, cost = grads(binding.seg_grad_noalloc, setup)
-        # same FP32 per-fiber terms; only the FP64 summation order and the order of the FP32
-        # atomic adds into the centroid gradient differ
+    for ga, gc, cost in got:
+        # the same FP32 per-fiber terms; the FP64 sums run in another fixed order, and the
+        # centroid gradient is an FP32 atomic sum here (seg_grad's is exact fixed point)
         assert cost == pytest.approx(ref_cost, rel=1e-9)
         np.testing.assert_allclose(ga, ref_a, rtol=1e-9, atol=1e-9)
         np.testing.assert_allclose(gc, ref_c, rtol=0, atol=1e-4)
-        if prev is not None:
-            assert np.array_equal(ga, prev[0]) and cost == prev[2]
-        prev = (ga, gc, cost)
+    assert np.array_equal(got[0][0], got[1][0]) and got[0][2] == got[1][2]
 
 
 def test_noalloc_rejects_oversized_call(setup):
