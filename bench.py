@@ -43,8 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="best", choices=["best", "plain", "gemm_bf16", "gemm_tf32",
-                                                      "gemm_inv_bf16", "gemm_inv_tf32"])
+    p.add_argument("--mode", default="best", choices=["best", *MODES])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--config", type=int, default=None, help="tile-shape config (default: tuned)")
     p.add_argument("--n", type=int, default=None, help="override the fiber count")
@@ -213,17 +212,28 @@ def _has_cuda():
 
 
 # ----------------------------------------------------------------------------- our arm
-MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32")
+MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled")
 KERNEL_NAME = {"plain": "k_label_plain", "gemm_screen": "k_gemm_screen",
+               "cull_screen": "k_culled_screen",
                "gemm_exact": "k_exact_blocks", "gemm_prep": "k_prep_a",
                "gemm_sort": "k_bin_count", "gemm_finalize": "k_finalize"}
-LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact",
+LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "cull_screen", "gemm_exact",
                 "gemm_finalize")
 # kernels the library launches inside each profiled scope (the sort is a count, two scans and a
 # scatter; the prep scope holds the fiber operand, the tile boxes and the active-block masks;
 # the finalize scope the overflow rescan and the label write)
 KERNELS_PER_SLOT = {"plain": 1, "gemm_sort": 4, "gemm_prep": 3, "gemm_screen": 1,
-                    "gemm_exact": 1, "gemm_finalize": 2}
+                    "cull_screen": 1, "gemm_exact": 1, "gemm_finalize": 2}
+
+
+def kernels_per_slot(mode: str, slot: str) -> int:
+    """Kernels one profiled scope launches (the culled mode's prep has no block-mask kernel)."""
+    return KERNELS_PER_SLOT[slot] - (1 if mode == "plain_culled" and slot == "gemm_prep" else 0)
+
+
+def dtype_of(mode: str) -> str:
+    return "f32" if mode in ("plain", "plain_culled") else \
+        ("bf16+f32" if mode.endswith("bf16") else "tf32+f32")
 
 
 def time_mode(binding, at, fib, labels, dst, mode, steps, warmup, stream, world, dist, dev):
@@ -252,8 +262,8 @@ def time_mode(binding, at, fib, labels, dst, mode, steps, warmup, stream, world,
     for k in LAUNCH_SLOTS:
         c, t = binding.seg_profile_read(at, k)
         if c:
-            kern[k] = {"launches": c * KERNELS_PER_SLOT[k], "ms_per_step": t / c}
-            launches += c * KERNELS_PER_SLOT[k]
+            kern[k] = {"launches": c * kernels_per_slot(mode, k), "ms_per_step": t / c}
+            launches += c * kernels_per_slot(mode, k)
     binding.seg_profile_enable(at, False)
     t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if world > 1:
@@ -401,6 +411,14 @@ def main():
                              "algorithmic": f"2 x K={kdim} x {st['screened']} pairs in the "
                                             f"computed blocks (of {st['pairs']}; the rest "
                                             f"culled on centre-point boxes)"}
+            elif kname == "cull_screen":
+                st = r["gemm_stats"]
+                alg = 6.0 * st["screened"]
+                mr[kname] = {"bound": "alu", "achieved": alg / sec / 1e12, "peak": alu_peak,
+                             "unit": "TFLOP/s", "peak_source": alu_src,
+                             "algorithmic": f"test1 in dot-product form (3 FMA = 6 flop) x "
+                                            f"{st['screened']} pairs in the blocks kept by the "
+                                            f"centre-point culling (of {st['pairs']})"}
             elif kname == "gemm_exact":
                 st = r["gemm_stats"]
                 alg = 8.0 * st["point_distances"]
@@ -423,8 +441,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if head == "plain" else
-                     ("bf16+f32" if head.endswith("bf16") else "tf32+f32"),
+            "dtype": dtype_of(head),
             "data": "synthetic",
             "config": {"workload": args.workload, "fibers": n, "centroids": atlas_np.M,
                        "bundles": atlas_np.B, "points": 21, "mode": head,
@@ -478,8 +495,7 @@ def run_batch(args, world, rank, dev, dist):
                           world * total / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                           "higher_is_better": True, "scaling": "weak",
-                          "dtype": "f32" if mode == "plain" else
-                                   ("bf16+f32" if mode.endswith("bf16") else "tf32+f32"),
+                          "dtype": dtype_of(mode),
                           "data": "synthetic",
                           "config": {"workload": args.workload, "subjects": 16,
                                      "fibers": total, "mode": mode,

@@ -74,7 +74,14 @@ typedef enum {
      * threshold of the block (d_ME >= the centre points' distance); they take at most 32,768
      * operand columns (2M directional, M orientation-free). */
     SEG_MODE_GEMM_INV_BF16 = 3,
-    SEG_MODE_GEMM_INV_TF32 = 4
+    SEG_MODE_GEMM_INV_TF32 = 4,
+    /* Spatial culling without the tensor cores: the GEMM modes' locality sort and centre-point
+     * block culling (32-fiber groups x 32-centroid chunks), then test1 (the centre point,
+     * Section 2.3) on CUDA cores for every pair of the remaining blocks, then the same exact
+     * test (both orientations) on the pairs that pass. Labels and distances equal
+     * SEG_MODE_PLAIN's. The culling is not in the paper (its Section 2.4 "data locality" is a
+     * cache argument); it is reported as its own algorithmic mode. */
+    SEG_MODE_PLAIN_CULLED = 5
 } seg_mode;
 
 typedef struct seg_atlas seg_atlas; /* opaque; owns its device copies of the atlas */
@@ -221,7 +228,8 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
  * seg_profile_read waits for those events and returns, for one kernel name, the number of
  * launches and their summed duration in milliseconds since profiling was (re)enabled.
  * Kernel names: "plain", "batch", "gemm_sort", "gemm_prep" (their launches precede the
- * screen), "gemm_screen", "gemm_exact", "gemm_finalize", "grad". Enabling (or disabling) clears what was recorded.
+ * screen), "gemm_screen", "cull_screen" (SEG_MODE_PLAIN_CULLED's test1 screen), "gemm_exact",
+ * "gemm_finalize", "grad". Enabling (or disabling) clears what was recorded.
  */
 seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable);
 seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launches,
@@ -257,11 +265,11 @@ seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survi
 
 /*
  * Diagnostic of the tensor-core prune (not in the paper): run the locality sort, the block
- * culling and the screen of a GEMM mode on n fibers and return the pairs the screen keeps for
+ * culling and the screen of a GEMM mode (or SEG_MODE_PLAIN_CULLED's test1 screen) on n fibers and return the pairs the screen keeps for
  * the exact test, instead of labels. d_bits is device uint32 [n][words_per_fiber], overwritten:
  * bit k of fiber f's row is set when the screen keeps column k for f, where k = 2 c + o for
  * the directional modes (c the caller's centroid index, o = 0 direct, 1 reversed) and k = c for
- * the orientation-free modes. words_per_fiber >= ceil(2M / 32) (directional) or ceil(M / 32).
+ * the orientation-free modes and SEG_MODE_PLAIN_CULLED. words_per_fiber >= ceil(2M / 32) (directional) or ceil(M / 32).
  * Every pair whose float32 exact test passes (d_o^2 <= theta^2) is kept; seg_gemm_stats reports
  * the screen's counters afterwards (overflow_fibers > 0 means survivors of those fibers were
  * dropped for lack of record space and the output is incomplete for them).

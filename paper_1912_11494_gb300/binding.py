@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_PKG, "libseg.so")
 SEG_OK = 0
 STATUS_NAMES = {0: "SEG_OK", 1: "SEG_ERR_INVALID_ARG", 2: "SEG_ERR_CUDA", 3: "SEG_ERR_OOM",
                 4: "SEG_ERR_UNSUPPORTED", 5: "SEG_ERR_TIMEOUT", 6: "SEG_ERR_OVERFLOW"}
-MODES = {"plain": 0, "gemm_bf16": 1, "gemm_tf32": 2, "gemm_inv_bf16": 3, "gemm_inv_tf32": 4}
+MODES = {"plain": 0, "gemm_bf16": 1, "gemm_tf32": 2, "gemm_inv_bf16": 3, "gemm_inv_tf32": 4,
+         "plain_culled": 5}
 NPTS = 21
 
 # Every entry point the header declares: (name, restype, argtypes).
@@ -246,7 +247,8 @@ def seg_gemm_screen_bits(atlas: Atlas, fibers, mode, stream=None):
     2c+o for directional modes, c for orientation-free ones, caller's centroid numbering)."""
     fib = _dev(fibers, torch.float32, "fibers").contiguous()
     m = _mode(mode)
-    cols = atlas.M if m in (MODES["gemm_inv_bf16"], MODES["gemm_inv_tf32"]) else 2 * atlas.M
+    cols = atlas.M if m in (MODES["gemm_inv_bf16"], MODES["gemm_inv_tf32"],
+                            MODES["plain_culled"]) else 2 * atlas.M
     words = (cols + 31) // 32
     bits = torch.empty((fib.shape[0], words), dtype=torch.int32, device=fib.device)
     _check(lib().seg_gemm_screen_bits(atlas.handle, _ptr(fib), int(fib.shape[0]), m,
@@ -270,8 +272,8 @@ def seg_gemm_stats(atlas: Atlas):
                 point_distances=d.value)
 
 
-PROFILED_KERNELS = ("plain", "batch", "gemm_sort", "gemm_prep", "gemm_screen", "gemm_exact",
-                    "gemm_finalize", "grad")
+PROFILED_KERNELS = ("plain", "batch", "gemm_sort", "gemm_prep", "gemm_screen", "cull_screen",
+                    "gemm_exact", "gemm_finalize", "grad")
 
 
 def seg_profile_enable(atlas: Atlas, enable: bool = True):

@@ -41,6 +41,8 @@
 // the innermost midpoint into g = c / sqrt(2) + s_9, which leaves 30 features and the pad column
 // within K = 32: half the tensor-core work of the 64-wide directional operands. Survivors are
 // checked in both orientations.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -391,6 +393,7 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
     const float c1 = __double2float_rd(0.5 * (1.0 - kappa_of(FMT)) - 1e-5);
     const float n2lo = __fmul_rd(n2, 0.999996f);
     alpha[i] = finite ? __fmaf_rd(n2lo, c1, -0.005f) : INFINITY;
+    if (FMT == 0) return;  // SEG_MODE_PLAIN_CULLED: no tensor-core operand
     __syncwarp();  // every lane has its input row in registers: reuse the buffer for output
     uint32_t* so = s_buf[w];
     constexpr int KE = INV ? KE_INV : KE_DIR;     // row: KE - 1 values, then the pad column 1
@@ -529,7 +532,7 @@ __global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, in
 // Spatial-order copies of the atlas for the GEMM modes (centroid rows point-major: point i as
 // the float4 (x, y, z, 0), CROW4 per row).
 __global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float4* cen_sp,
-                               float* thr2_sp, float4* ctr_sp) {
+                               float* thr2_sp, float4* ctr_sp, float4* scr_sp) {
     const int c = blockIdx.x * blockDim.y + threadIdx.y;
     if (c >= at.M) return;
     const int s = sp_s[c];
@@ -540,6 +543,7 @@ __global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float
                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (threadIdx.x == 0) {
         thr2_sp[c] = at.thr2[s];
+        scr_sp[c] = at.scr2[s];
         ctr_sp[c] = make_float4(src[3 * CENTRE], src[3 * CENTRE + 1], src[3 * CENTRE + 2],
                                 at.thr2[s]);
     }
@@ -906,6 +910,85 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// ---- SEG_MODE_PLAIN_CULLED: test1 on CUDA cores over the culled blocks ---------------------------
+// The same locality order and centre-point culling as the tensor-core modes, with the paper's own
+// first discarding test in place of the GEMM bound: test1 (Section 2.3, the centre point, shared
+// by both orientations) in the plain kernel's dot-product form, a'.b' + (theta^2 - |b'|^2)/2 >=
+// |a'|^2 / 2 with its rounding slack (so every pair the exact FP32 test1 accepts is kept). One
+// warp per 32-fiber group, lane = fiber: the 32-centroid chunks whose box is within reach of the
+// group's centre-point box are tested (a warp ballot over 32 chunks at a time), each chunk's 32
+// screen rows staged in shared memory and read as broadcasts; the surviving columns of a chunk
+// form a block record in the tensor-core modes' format (orientation-free columns: spatial
+// centroid index), checked by the same exact kernel.
+constexpr int CS_WARPS = 8;
+
+__global__ void __launch_bounds__(CS_WARPS * 32)
+k_culled_screen(long long n, long long n_groups, AtlasView at, GemmScratch g,
+                const float4* __restrict__ scr_sp, const float4* __restrict__ ubox,
+                const float4* __restrict__ tbox, int n_chunks) {
+    __shared__ float4 s_q[CS_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    SlotGrab slots;
+    unsigned long long surv = 0, screened = 0;
+    const long long W = (long long)gridDim.x * CS_WARPS;
+    for (long long gi = (long long)blockIdx.x * CS_WARPS + w; gi < n_groups; gi += W) {
+        const long long f = gi * 32 + lane;
+        float x = 0.0f, y = 0.0f, z = 0.0f, h = NAN;  // NaN never passes
+        if (f < n && g.key[f] != NAN_KEY) {
+            const float* c = g.fs + (size_t)f * CROW + 3 * CENTRE;
+            x = c[0] - at.c0x;
+            y = c[1] - at.c0y;
+            z = c[2] - at.c0z;
+            const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+            h = 0.5f * r2 - 1e-5f * r2 - 1e-3f;
+        }
+        const float4 lo = __ldg(ubox + 2 * gi), hi = __ldg(ubox + 2 * gi + 1);
+        if (!(lo.x <= hi.x)) continue;  // no finite fiber in the group
+        const UnitBox box{lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+        for (int k0 = 0; k0 < n_chunks; k0 += 32) {
+            const int c = k0 + lane;
+            unsigned act = __ballot_sync(0xffffffffu, c < n_chunks && block_active(box, tbox, c));
+            while (act) {
+                const int cc = k0 + __ffs(act) - 1;
+                act &= act - 1;
+                const int j = 32 * cc + lane;
+                __syncwarp();
+                s_q[w][lane] = j < at.M ? __ldg(scr_sp + j) : make_float4(0.f, 0.f, 0.f, -INFINITY);
+                __syncwarp();
+                unsigned m = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float4 q = s_q[w][i];
+                    const float t = fmaf(z, q.z, fmaf(y, q.y, fmaf(x, q.x, q.w)));
+                    m |= (t >= h ? 1u : 0u) << i;
+                }
+                screened += 32;
+                if (!__any_sync(0xffffffffu, m != 0u)) continue;
+                surv += __popc(m);
+                const unsigned long long b = slots.take(g, lane);
+                if ((long long)b < g.cap) {
+                    g.mask[b * 32 + lane] = m;
+                    if (lane == 0) g.hdr[b] = make_uint2((unsigned)(gi * 32), (unsigned)(32 * cc));
+                } else if (m != 0u && g.flag[f] == 0) {
+                    g.flag[f] = 1;  // no room: the fiber is rescanned exactly
+                    atomicAdd(g.cnt + 1, 1ull);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    slots.close(g, lane);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        surv += __shfl_down_sync(0xffffffffu, surv, off);
+        screened += __shfl_down_sync(0xffffffffu, screened, off);
+    }
+    if (lane == 0) {
+        if (surv) atomicAdd(g.cnt + 2, surv);
+        if (screened) atomicAdd(g.cnt + 3, screened);
+    }
 }
 
 // ---- exact test of the survivors, overflow rescan, finalize ------------------------------------
@@ -1363,14 +1446,15 @@ seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g
     if ((e = cudaMalloc(&g->sp_s, (size_t)at.M * sizeof(int))) ||
         (e = cudaMalloc(&g->cen_sp, (size_t)at.M * CROW4 * sizeof(float4))) ||
         (e = cudaMalloc(&g->thr2_sp, (size_t)at.M * sizeof(float))) ||
-        (e = cudaMalloc(&g->ctr_sp, (size_t)at.M * sizeof(float4))))
+        (e = cudaMalloc(&g->ctr_sp, (size_t)at.M * sizeof(float4))) ||
+        (e = cudaMalloc(&g->scr_sp, (size_t)at.M * sizeof(float4))))
         return cuda_fail(e, "gemm spatial order");
     // the host array lives until the caller synchronizes the stream
     if ((e = cudaMemcpyAsync(g->sp_s, sp_host, (size_t)at.M * sizeof(int), cudaMemcpyHostToDevice,
                              st)))
         return cuda_fail(e, "gemm spatial order");
     k_prep_spatial<<<(at.M + 7) / 8, dim3(32, 8), 0, st>>>(at, g->sp_s, g->cen_sp, g->thr2_sp,
-                                                          g->ctr_sp);
+                                                          g->ctr_sp, g->scr_sp);
     g->cols = 2 * at.M;
     g->cols_pad = (g->cols + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
     if ((e = cudaMalloc(&g->b_bf16, (size_t)g->cols_pad * 64 * 2)) ||
@@ -1401,6 +1485,7 @@ void free_gemm_atlas(GemmAtlas* g) {
     cudaFree(g->cen_sp);
     cudaFree(g->thr2_sp);
     cudaFree(g->ctr_sp);
+    cudaFree(g->scr_sp);
     cudaFree(g->stats);
     *g = GemmAtlas{};
 }
@@ -1409,8 +1494,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
                       const float* fib, long long n, int mode, int* labels, float* dist,
                       int* cidx, unsigned char* orient, cudaStream_t st, int config,
                       Profiler* prof, unsigned* dbg_bits, long long dbg_words) {
+    const bool culled = mode == SEG_MODE_PLAIN_CULLED;  // test1 on CUDA cores, no operand
     const bool tf32 = mode == SEG_MODE_GEMM_TF32 || mode == SEG_MODE_GEMM_INV_TF32;
-    const bool inv = mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
+    const bool inv = culled || mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
     const int fmt = tf32 ? 2 : 1;
     const int cols = inv ? ga->cols_inv : ga->cols;
     const int cols_pad = inv ? ga->cols_inv_pad : ga->cols_pad;
@@ -1426,7 +1512,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
     const int n_chunks = cols_pad / 32;
     const int awords = (n_chunks + 63) / 64;
-    if (awords > MAXW)
+    if (!culled && awords > MAXW)
         return fail(SEG_ERR_UNSUPPORTED,
                     "seg_label: %d operand columns exceed the GEMM modes' limit of %d", cols_pad,
                     32 * 64 * MAXW);
@@ -1434,7 +1520,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     // per 32 fibers + slack (fibers past the room are rescanned exactly)
     long long cap = n_pad / 32 * 16 + 65536;
     if (ga->cap_limit > 0 && ga->cap_limit < cap) cap = ga->cap_limit;
-    const size_t elem = tf32 ? 4 : 2;
+    const size_t elem = culled ? 0 : tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * sh.ke * elem);
     const size_t off_key = off_alpha + align256((size_t)n_pad * 4);
     const size_t off_flag = off_key + align256((size_t)n * 8);
@@ -1485,8 +1571,8 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
 
     cudaError_t e = cudaSuccess;
     CUtensorMap ta, tb;
-    if (!make_tmap(&ta, g.a, n_pad, fmt, sh.ke, 128) ||
-        !make_tmap(&tb, bop, cols_pad, fmt, sh.ke, sh.N)) {
+    if (!culled && (!make_tmap(&ta, g.a, n_pad, fmt, sh.ke, 128) ||
+                    !make_tmap(&tb, bop, cols_pad, fmt, sh.ke, sh.N))) {
         scratch_release(scratch, st);
         return fail(SEG_ERR_CUDA, "seg_label: cuTensorMapEncodeTiled failed");
     }
@@ -1506,8 +1592,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
         const unsigned pb = (unsigned)((n_pad + rows_per_block - 1) / rows_per_block);
-        auto prep = tf32 ? (inv ? k_prep_a<2, true> : k_prep_a<2, false>)
-                         : (inv ? k_prep_a<1, true> : k_prep_a<1, false>);
+        auto prep = culled ? k_prep_a<0, false>
+                    : tf32 ? (inv ? k_prep_a<2, true> : k_prep_a<2, false>)
+                           : (inv ? k_prep_a<1, true> : k_prep_a<1, false>);
         prep<<<pb, PREP_WARPS * 32, 0, st>>>(fib, perm, n, n_pad, at, g.a, g.alpha, g.key, g.fs,
                                              ubox);
         // centroids per 32-column chunk: 32 (orientation-free) or 16 (directional)
@@ -1515,15 +1602,24 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         if (!e)
             k_tile_box<<<(n_chunks + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M, inv ? 32 : 16,
                                                               n_chunks, tbox);
-        if (!e)
+        if (!e && !culled)
             k_block_mask<<<(unsigned)((n_units + 3) / 4), 128, 0, st>>>(
                 ubox, tbox, n_units, sh.R, n_chunks, awords,
                 reinterpret_cast<unsigned long long*>(b8 + off_amask));
         e = cudaGetLastError();
     }
     if (!e) {
-        ProfScope ps(prof, PROF_GEMM_SCREEN, st);
-        e = dispatch_screen(sh, ta, tb, n_units, n_tiles, cols, g, at.status, sms, st);
+        ProfScope ps(prof, culled ? PROF_CULL_SCREEN : PROF_GEMM_SCREEN, st);
+        if (culled) {
+            const long long n_groups = n_pad / 32;
+            k_culled_screen<<<(unsigned)std::min<long long>((n_groups + CS_WARPS - 1) / CS_WARPS,
+                                                            (long long)sms * 8),
+                              CS_WARPS * 32, 0, st>>>(n, n_groups, at, g, ga->scr_sp, ubox, tbox,
+                                                      n_chunks);
+            e = cudaGetLastError();
+        } else {
+            e = dispatch_screen(sh, ta, tb, n_units, n_tiles, cols, g, at.status, sms, st);
+        }
     }
     if (!e && dbg_bits) {  // diagnostic: the screen's survivors instead of labels
         e = cudaMemsetAsync(dbg_bits, 0, (size_t)n * dbg_words * 4, st);

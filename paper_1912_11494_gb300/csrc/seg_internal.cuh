@@ -17,7 +17,7 @@ seg_status cuda_fail(cudaError_t e, const char* what);
 
 // Event-pair timing of the library's kernels (seg_profile_enable / seg_profile_read).
 enum ProfSlot { PROF_PLAIN = 0, PROF_BATCH, PROF_GEMM_PREP, PROF_GEMM_SCREEN, PROF_GEMM_EXACT,
-                PROF_GEMM_FINAL, PROF_GRAD, PROF_GEMM_SORT, PROF_SLOTS };
+                PROF_GEMM_FINAL, PROF_GRAD, PROF_GEMM_SORT, PROF_CULL_SCREEN, PROF_SLOTS };
 struct Profiler {
     bool enabled = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;  // reusable events
@@ -70,6 +70,7 @@ struct GemmAtlas {
     float4* cen_sp = nullptr; // [M][21] centroid rows in spatial order, point-major
     float* thr2_sp = nullptr; // [M] theta^2 in spatial order
     float4* ctr_sp = nullptr; // [M] centre point and theta^2 in spatial order
+    float4* scr_sp = nullptr; // [M] the test1 screen row (AtlasView::scr2) in spatial order
     long long* stats = nullptr;  // [5] pairs, survivors, overflow fibers, screened pairs,
                                  // point distances of the exact re-check
     long long cap_limit = 0;     // caller's limit on survivor block records (0: none)

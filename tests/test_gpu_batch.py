@@ -44,7 +44,8 @@ def batch(at, fibs, mode, with_dist=True):
             [d.cpu().numpy() for d in dists] if with_dist else None)
 
 
-@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16"])
+@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16",
+                                  "plain_culled"])
 def test_batch_equals_single_calls(env, mode):
     dev, a, at = env
     fibs = subjects(a, [0, 1, 33, 1000, 5000, 257, 31], 100, dev)
