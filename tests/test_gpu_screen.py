@@ -5,9 +5,10 @@ BF16/TF32 lower bound with its rounding margin does not exceed the threshold, an
 blocks whose centre-point boxes are out of reach (SEG_MODE_PLAIN_CULLED keeps the pairs that
 pass test1 in dot-product form, with its rounding slack, in the blocks it does not cull).
 Labels only stay exact if no pair the FP32 exact test would accept is ever dropped. This test
-reads the pairs the screen kept, straight from the kernel, and checks them against FP64 d_ME from the oracle (Eq. 2): every pair whose
-FP64 distance in an orientation is within theta (1 + 4e-6) must be kept (the FP32 exact test
-accepts d^2 <= theta^2 computed in FP32, i.e. FP64 distances up to about theta (1 + 1e-6)).
+reads the pairs the screen kept, straight from the kernel, and checks them against FP64 d_ME
+from the oracle (Eq. 2): every pair whose FP64 distance in an orientation is within
+theta (1 + 4e-6) must be kept (the FP32 exact test accepts d^2 <= theta^2 computed in FP32,
+i.e. FP64 distances up to about theta (1 + 1e-6)).
 
 Inputs: the 10,000 x 1,000 workload's atlas with 2,048 of its fibers, plus adversarial fibers
 built to sit on the bound: a centroid moved rigidly by a vector of length theta (1 - 1e-6), so
