@@ -47,7 +47,7 @@ typedef enum {
     SEG_ERR_CUDA = 2,        /* a CUDA runtime call failed; seg_last_error() has the text */
     SEG_ERR_OOM = 3,         /* device allocation failed */
     SEG_ERR_UNSUPPORTED = 4, /* mode or device not supported (needs sm_103a), or an atlas too
-                              * large for a GEMM mode (more than 32,768 operand columns) */
+                              * large for a GEMM mode (more than 131,072 operand columns) */
     SEG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up; results of that call invalid */
     SEG_ERR_OVERFLOW = 6     /* a fixed-capacity device list overflowed and was not recovered */
 } seg_status;
@@ -71,7 +71,7 @@ typedef enum {
      * All GEMM modes sort the fibers by the 2 mm cell of their centre point (cells along a
      * Hilbert curve; the centroid columns follow the same order) and skip the
      * (128-fiber, 32-column) blocks whose centre-point boxes are farther apart than every
-     * threshold of the block (d_ME >= the centre points' distance); they take at most 32,768
+     * threshold of the block (d_ME >= the centre points' distance); they take at most 131,072
      * operand columns (2M directional, M orientation-free). */
     SEG_MODE_GEMM_INV_BF16 = 3,
     SEG_MODE_GEMM_INV_TF32 = 4,

@@ -448,7 +448,7 @@ __device__ inline bool block_active(const UnitBox& b, const float4* __restrict__
     return !(lb2 > lo.w * 1.0001f + 1e-3f);  // lo.w: max theta^2 of the tile
 }
 
-constexpr int MAXW = 16;  // mask words per unit: at most 1024 chunks (32768 columns)
+constexpr int MAXW = 64;  // mask words per unit: at most 4096 chunks (131,072 columns)
 
 // The next tile with an active chunk in `bits` (word wd of a unit's chunk mask, CPT chunks per
 // tile); clears that tile's bits.
@@ -824,25 +824,31 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // each unit's alpha values and mask words (one per lane, handed out by shuffles) are
         // loaded one unit ahead, so that a unit never starts on a memory round trip
         float aln[4];
-        unsigned long long mwn;
+        unsigned long long mwn[2];  // mask words lane and lane + 32 of the next unit
         auto load_unit = [&](long long u) {
 #pragma unroll
             for (int r = 0; r < 4; ++r)
                 aln[r] = r < R && u < n_units
                              ? __ldg(g.alpha + (u * R + r) * 128 + 32 * q + lane)
                              : INFINITY;
-            mwn = u < n_units && lane < g.awords ? __ldg(g.amask + u * g.awords + lane) : 0ull;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                mwn[h] = u < n_units && lane + 32 * h < g.awords
+                             ? __ldg(g.amask + u * g.awords + lane + 32 * h)
+                             : 0ull;
         };
         load_unit(blockIdx.x);
         for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
             float al[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) al[r] = aln[r];
-            const unsigned long long mword = mwn;
+            const unsigned long long mword0 = mwn[0], mword1 = mwn[1];
             load_unit(u + gridDim.x);
             const unsigned fib0 = (unsigned)(u * R * 128 + 32 * q + lane);
             for (int wd = 0; wd < g.awords && ok; ++wd)
-            for (unsigned long long bits = __shfl_sync(0xffffffffu, mword, wd); bits;) {
+            for (unsigned long long bits =
+                     __shfl_sync(0xffffffffu, wd < 32 ? mword0 : mword1, wd & 31);
+                 bits;) {
                 const unsigned long long word = bits;
                 const int t = next_tile<CPT>(bits, wd);
                 // this tile's chunk bits: chunk c of the tile's columns may hold survivors
@@ -1437,9 +1443,14 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 int gemm_num_configs() { return kNumShapes; }
 
-seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g,
-                           cudaStream_t st) {
+seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, int max_per_bundle,
+                           GemmAtlas* g, cudaStream_t st) {
     cudaError_t e;
+    // A 32-fiber group inside a bundle keeps most of that bundle's centroids in both
+    // orientations: about 2 * max_per_bundle / 32 directional chunks, contiguous in the spatial
+    // order; twice that plus slack, and never less than 16 (atlases shaped like the paper's
+    // 20-centroid bundles need about 3.4).
+    g->rec_per_group = std::max(16, 2 * ((2 * max_per_bundle + 31) / 32) + 8);
     if ((e = cudaMalloc(&g->stats, 5 * sizeof(long long))) ||
         (e = cudaMemsetAsync(g->stats, 0, 5 * sizeof(long long), st)))
         return cuda_fail(e, "gemm stats");
@@ -1516,9 +1527,9 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         return fail(SEG_ERR_UNSUPPORTED,
                     "seg_label: %d operand columns exceed the GEMM modes' limit of %d", cols_pad,
                     32 * 64 * MAXW);
-    // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for 16
-    // per 32 fibers + slack (fibers past the room are rescanned exactly)
-    long long cap = n_pad / 32 * 16 + 65536;
+    // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for
+    // rec_per_group per 32 fibers + slack (fibers past the room are rescanned exactly)
+    long long cap = n_pad / 32 * ga->rec_per_group + 65536;
     if (ga->cap_limit > 0 && ga->cap_limit < cap) cap = ga->cap_limit;
     const size_t elem = culled ? 0 : tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * sh.ke * elem);

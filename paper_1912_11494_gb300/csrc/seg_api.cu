@@ -288,7 +288,10 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
     a->view.bundle = a->bundle;
     a->view.perm = a->perm;
     a->view.status = a->status;
-    seg_status s = prep_gemm_atlas(a->view, sp.data(), &a->gemm, st);
+    int max_per_bundle = 0;  // (cnt[b] now ends bundle b: the sort advanced it)
+    for (int b = 0; b < B; ++b)
+        max_per_bundle = std::max(max_per_bundle, cnt[b] - (b ? cnt[b - 1] : 0));
+    seg_status s = prep_gemm_atlas(a->view, sp.data(), max_per_bundle, &a->gemm, st);
     if (s != SEG_OK) {
         free_atlas(a);
         return s;

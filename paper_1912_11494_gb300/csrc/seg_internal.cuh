@@ -74,9 +74,11 @@ struct GemmAtlas {
     long long* stats = nullptr;  // [5] pairs, survivors, overflow fibers, screened pairs,
                                  // point distances of the exact re-check
     long long cap_limit = 0;     // caller's limit on survivor block records (0: none)
+    int rec_per_group = 16;      // default room for block records per 32 fibers (from the
+                                 // atlas's largest bundle)
 };
-seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, GemmAtlas* g,
-                           cudaStream_t st);
+seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, int max_per_bundle,
+                           GemmAtlas* g, cudaStream_t st);
 void free_gemm_atlas(GemmAtlas* g);
 int gemm_num_configs();
 seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, std::mutex* mu,

@@ -128,17 +128,30 @@ class Atlas:
         return int(self.thresholds.shape[0])
 
 
-def make_atlas(n_bundles: int, per_bundle: int = 20, seed: int = 1000, thr_lo: float = 5.0,
+def make_atlas(n_bundles: int, per_bundle=20, seed: int = 1000, thr_lo: float = 5.0,
                thr_hi: float = 8.0, sigma: float = 1.5, device="cpu") -> Atlas:
-    """Atlas of n_bundles x per_bundle centroids, bundle-major, thresholds U[thr_lo, thr_hi]."""
+    """Atlas of n_bundles bundles, bundle-major, thresholds U[thr_lo, thr_hi]; per_bundle is a
+    centroid count for every bundle or a sequence of n_bundles counts."""
     rng = _rng(seed)
     base = _random_curves(rng, n_bundles, device)
     thr = rng.uniform(thr_lo, thr_hi, size=n_bundles).astype(np.float32)
-    pert = rng.normal(0.0, sigma, size=(n_bundles, per_bundle, 4, 3))
-    ctrl = (base[:, None] + pert).reshape(-1, 4, 3)
+    counts = np.broadcast_to(np.asarray(per_bundle, dtype=np.int64), (n_bundles,))
+    if np.all(counts == counts[0]):
+        pert = rng.normal(0.0, sigma, size=(n_bundles, int(counts[0]), 4, 3))
+        ctrl = (base[:, None] + pert).reshape(-1, 4, 3)
+    else:
+        pert = rng.normal(0.0, sigma, size=(int(counts.sum()), 4, 3))
+        ctrl = np.repeat(base, counts, axis=0) + pert
     cen = _resample_ctrl(ctrl, device)
-    bundle_of = np.repeat(np.arange(n_bundles, dtype=np.int32), per_bundle)
+    bundle_of = np.repeat(np.arange(n_bundles, dtype=np.int32), counts)
     return Atlas(cen, bundle_of, thr, base)
+
+
+def whole_brain_counts(n_bundles: int = 62, total: int = 44_345) -> list[int]:
+    """Centroids per bundle of the whole-brain stress atlas: `total` centroids spread as evenly
+    as possible over `n_bundles` bundles (the paper's 62-bundle atlas has 44,345 centroids)."""
+    q, r = divmod(total, n_bundles)
+    return [q + 1] * r + [q] * (n_bundles - r)
 
 
 def make_subject(atlas: Atlas, n: int, bundle_frac: float, seed: int, sigma: float = 2.0,
@@ -201,13 +214,18 @@ WORKLOADS = {
                                   seed=2),
     # 1,000,000 fibers, 250 x 20 centroids, 70% bundle, after a random affine (seed 5).
     "affine1m_atlas5k": dict(n=1_000_000, bundles=250, bundle_frac=0.70, atlas_seed=1005, seed=5),
+    # The paper's headline subject size against an atlas shaped like its 62-bundle whole-brain
+    # atlas (44,345 centroids, Section 2.2), 75% bundle fibers.
+    "subject4145k_atlas44k": dict(n=4_145_000, bundles=62, per_bundle=whole_brain_counts(),
+                                  bundle_frac=0.75, atlas_seed=1006, seed=6),
 }
 
 
 def workload(name: str, n: int | None = None, device="cpu"):
     """(atlas, fibers) for a named workload; n overrides the fiber count (same seeds)."""
     w = WORKLOADS[name]
-    atlas = make_atlas(w["bundles"], seed=w["atlas_seed"], device=device)
+    atlas = make_atlas(w["bundles"], per_bundle=w.get("per_bundle", 20), seed=w["atlas_seed"],
+                       device=device)
     fib = make_subject(atlas, w["n"] if n is None else n, w["bundle_frac"], w["seed"],
                        device=device)
     return atlas, fib

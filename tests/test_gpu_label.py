@@ -293,17 +293,46 @@ def test_survivor_list_overflow_rescans_exactly(dev, mode):
 
 
 def test_gemm_column_limit(dev):
-    """The GEMM modes take at most 32,768 operand columns: 17,000 centroids exceed it in the
+    """The GEMM modes take at most 131,072 operand columns: 66,000 centroids exceed it in the
     directional layout (2M columns) but not in the orientation-free one (M columns)."""
-    a = synth.make_atlas(850, per_bundle=20, seed=53)
+    a = synth.make_atlas(3300, per_bundle=20, seed=53)
     fib = synth.make_subject(a, 500, 0.8, seed=54)
     at = make_atlas(a.centroids, a.bundle_of, a.thresholds, dev)
     with pytest.raises(binding.SegError):
         run(at, fib, dev, "gemm_bf16")
     ref = run(at, fib, dev, "plain")
-    got = run(at, fib, dev, "gemm_inv_bf16")
-    for x, y in zip(ref, got):
-        np.testing.assert_array_equal(x, y)
+    for mode in ("gemm_inv_bf16", "plain_culled"):
+        got = run(at, fib, dev, mode)
+        for x, y in zip(ref, got):
+            np.testing.assert_array_equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def whole_brain():
+    """A subject of 40,000 fibers against the atlas shaped like the paper's 62-bundle
+    whole-brain atlas (44,345 centroids: 88,690 directional columns)."""
+    return synth.workload("subject4145k_atlas44k", n=40_000)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_whole_brain_atlas_parity(dev, mode, whole_brain):
+    """Every mode on the 44,345-centroid atlas: bit-identical to the plain kernel, and every
+    fiber against the oracle."""
+    atlas_np, fib = whole_brain
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    got = run(at, fib, dev, mode)
+    if mode != "plain":
+        ref = run(at, fib, dev, "plain")
+        for x, y in zip(ref, got):
+            np.testing.assert_array_equal(x, y)
+        st = binding.seg_gemm_stats(at)
+        assert st["overflow_fibers"] == 0
+    else:
+        res = parity.compare_all(fib, atlas_np.centroids, atlas_np.bundle_of,
+                                 atlas_np.thresholds, *got)
+        assert res["labelled"] > 0.5 * len(fib)
+        print(f"\nwhole-brain atlas: {res['labelled']} of {res['n']} labelled, "
+              f"{res['mismatches']} near-tie label differences, {res['near_ties']} near-ties")
 
 
 def test_every_tile_shape_identical(dev, small_workload):
