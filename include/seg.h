@@ -147,12 +147,18 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
                           seg_mode mode, int32_t* h_labels, float* h_dist, void* stream);
 
 /*
- * Label nsubj subjects of uneven size in one persistent launch (not in the paper; the paper
- * labels one subject at a time, Section 3). Subject s has h_counts[s] >= 0 fibers at device
- * pointer h_fibers[s] and writes h_labels[s] (required) and h_dist[s] (array or entries may be
- * NULL). The pointer arrays are host memory read during the call. Results per subject equal
- * seg_label's. The launch sequence is captured once into a CUDA graph per (atlas, nsubj) and
- * replayed with a new work table; the first call per shape pays the capture.
+ * Label nsubj subjects of uneven size together (not in the paper; the paper labels one subject
+ * at a time, Section 3). Subject s has h_counts[s] >= 0 fibers at device pointer h_fibers[s]
+ * and writes h_labels[s] (required) and h_dist[s] (array or entries may be NULL). The pointer
+ * arrays are host memory read during the call. Results per subject equal seg_label's.
+ *  - SEG_MODE_PLAIN: one persistent launch over (subject, 32-fiber tile) work items.
+ *  - GEMM modes and SEG_MODE_PLAIN_CULLED: the subjects form one virtual array of fibers that
+ *    goes through the mode's launch sequence once (sorted and screened together).
+ * In every mode the launches are captured once into a CUDA graph and replayed; the graph is
+ * captured again when the mode, tile shape or subject count changes (and, in the GEMM and
+ * culled modes, the total fiber count or the atlas's scratch buffer). The work table is copied
+ * to the device on `stream` before each replay from one of two pinned buffers used by
+ * alternate calls, so a call waits on the host only for the table copy of two calls earlier.
  */
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,
                            const int64_t* h_counts, seg_mode mode, int32_t* const* h_labels,

@@ -233,11 +233,11 @@ __device__ inline unsigned cell_of(float v, float c0) {
     return t >= 0.0f ? (unsigned)fminf(t, (float)((1 << LOC_BITS) - 1)) : 0u;  // NaN -> 0
 }
 
-__global__ void k_bin_count(const float* __restrict__ fib, long long n, AtlasView at,
+__global__ void k_bin_count(FiberSrc src, long long n, AtlasView at,
                             unsigned* __restrict__ bin, unsigned* __restrict__ hist) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float* c = fib + i * NC + 3 * CENTRE;
+    const float* c = src.row(i) + 3 * CENTRE;
     const unsigned b = hilbert_index3(cell_of(__ldg(c), at.c0x), cell_of(__ldg(c + 1), at.c0y),
                                       cell_of(__ldg(c + 2), at.c0z));
     bin[i] = b;
@@ -318,7 +318,7 @@ constexpr int PREP_STRIDE = 65;
 
 template <int FMT, bool INV>
 __global__ void __launch_bounds__(PREP_WARPS * 32, 4)
-k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long long n,
+k_prep_a(FiberSrc fsrc, const unsigned* __restrict__ perm, long long n,
          long long n_pad, AtlasView at, void* __restrict__ out,
          float* __restrict__ alpha, unsigned long long* __restrict__ key,
          float* __restrict__ fs, float4* __restrict__ ubox) {
@@ -330,7 +330,7 @@ k_prep_a(const float* __restrict__ fib, const unsigned* __restrict__ perm, long 
     float* si = reinterpret_cast<float*>(s_buf[w]);
     const unsigned src_row = lane < rows_in ? __ldg(perm + r0 + lane) : 0u;
     for (int r = 0; r < rows_in; ++r) {  // all 63 x 32 copies in flight at once
-        const float* src = fib + (size_t)__shfl_sync(0xffffffffu, src_row, r) * NC;
+        const float* src = fsrc.row(__shfl_sync(0xffffffffu, src_row, r));
         cp_async4(si + r * PREP_STRIDE + lane, src + lane);
         if (lane < NC - 32) cp_async4(si + r * PREP_STRIDE + 32 + lane, src + 32 + lane);
     }
@@ -1292,9 +1292,10 @@ __global__ void k_overflow_rescan(long long n, AtlasView at, GemmScratch g) {
         if (g.flag[f]) rescan_fiber(f, at, g);
 }
 
-// Labels and distances in the caller's order.
-__global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __restrict__ labels,
-                           float* __restrict__ dist, int* __restrict__ cidx,
+// Labels and distances in the caller's order (for several subjects: into each subject's
+// arrays; cidx and orient are not written then).
+__global__ void k_finalize(long long n, AtlasView at, GemmScratch g, FiberSrc src, int* labels,
+                           float* dist, int* __restrict__ cidx,
                            unsigned char* __restrict__ orient, long long pairs,
                            long long* __restrict__ stats) {
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1307,7 +1308,15 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, int* __rest
     }
     if (f >= n) return;
     const unsigned long long k = g.key[f];
-    const unsigned o = g.perm[f];  // results go to the caller's order
+    long long o = g.perm[f];  // results go to the caller's order
+    if (src.table) {
+        const BatchEntry& e = src.table[src.subject(o)];
+        labels = e.labels;
+        dist = e.dist;
+        cidx = nullptr;
+        orient = nullptr;
+        o -= e.first;
+    }
     if (k == NAN_KEY || k == ~0ull) {
         labels[o] = -1;
         if (dist) dist[o] = k == NAN_KEY ? NAN : INFINITY;
@@ -1501,13 +1510,27 @@ void free_gemm_atlas(GemmAtlas* g) {
     *g = GemmAtlas{};
 }
 
-seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, std::mutex* mu,
-                      const float* fib, long long n, int mode, int* labels, float* dist,
-                      int* cidx, unsigned char* orient, cudaStream_t st, int config,
-                      Profiler* prof, unsigned* dbg_bits, long long dbg_words) {
-    const bool culled = mode == SEG_MODE_PLAIN_CULLED;  // test1 on CUDA cores, no operand
-    const bool tf32 = mode == SEG_MODE_GEMM_TF32 || mode == SEG_MODE_GEMM_INV_TF32;
-    const bool inv = culled || mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
+// One GEMM-mode call over n fibers: sizes, the scratch layout and the tensor maps.
+struct GemmCall {
+    bool culled, tf32, inv;
+    GemmShape sh;
+    long long n, n_pad, n_units;
+    int cols, n_tiles, n_chunks, awords, sms;
+    GemmScratch g;
+    unsigned *perm, *bin, *hist, *top;
+    float4 *ubox, *tbox;
+    unsigned long long* amask;
+    CUtensorMap ta, tb;
+};
+
+// Sizes the call, takes the atlas's scratch (the caller holds the atlas mutex and releases the
+// scratch on `st` once the call's work is enqueued) and encodes the tensor maps.
+seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, long long n,
+                      int mode, int config, cudaStream_t st, GemmCall* c) {
+    c->culled = mode == SEG_MODE_PLAIN_CULLED;  // test1 on CUDA cores, no operand
+    c->tf32 = mode == SEG_MODE_GEMM_TF32 || mode == SEG_MODE_GEMM_INV_TF32;
+    c->inv = c->culled || mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
+    const bool culled = c->culled, tf32 = c->tf32, inv = c->inv;
     const int fmt = tf32 ? 2 : 1;
     const int cols = inv ? ga->cols_inv : ga->cols;
     const int cols_pad = inv ? ga->cols_inv_pad : ga->cols_pad;
@@ -1518,7 +1541,6 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const long long rows_per_unit = 128LL * sh.R;
     const long long n_units = (n + rows_per_unit - 1) / rows_per_unit;
     const long long n_pad = n_units * rows_per_unit;
-    const int n_tiles = cols_pad / sh.N;
     if (n_pad >= (1LL << 32))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld too large for the GEMM modes", n);
     const int n_chunks = cols_pad / 32;
@@ -1548,16 +1570,14 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const size_t off_mask = off_hdr + align256((size_t)cap * 8);
     const size_t bytes = off_mask + (size_t)cap * 128;
 
-    int dev = 0, sms = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-
-    std::lock_guard<std::mutex> lock(*mu);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
     void* base = nullptr;
     seg_status s = scratch_acquire(scratch, bytes, st, &base);
     if (s != SEG_OK) return s;
     unsigned char* b8 = static_cast<unsigned char*>(base);
-    GemmScratch g;
+    GemmScratch& g = c->g;
     g.a = b8;
     g.alpha = reinterpret_cast<float*>(b8 + off_alpha);
     g.key = reinterpret_cast<unsigned long long*>(b8 + off_key);
@@ -1565,86 +1585,102 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     g.cnt = reinterpret_cast<unsigned long long*>(b8 + off_cnt);
     g.hdr = reinterpret_cast<uint2*>(b8 + off_hdr);
     g.mask = reinterpret_cast<unsigned*>(b8 + off_mask);
-    unsigned* perm = reinterpret_cast<unsigned*>(b8 + off_perm);
-    unsigned* bin = reinterpret_cast<unsigned*>(b8 + off_bin);
-    unsigned* hist = reinterpret_cast<unsigned*>(b8 + off_hist);
-    unsigned* top = reinterpret_cast<unsigned*>(b8 + off_top);
-    g.perm = perm;
+    c->perm = reinterpret_cast<unsigned*>(b8 + off_perm);
+    c->bin = reinterpret_cast<unsigned*>(b8 + off_bin);
+    c->hist = reinterpret_cast<unsigned*>(b8 + off_hist);
+    c->top = reinterpret_cast<unsigned*>(b8 + off_top);
+    g.perm = c->perm;
     g.fs = reinterpret_cast<float*>(b8 + off_fs);
-    float4* ubox = reinterpret_cast<float4*>(b8 + off_ubox);
-    float4* tbox = reinterpret_cast<float4*>(b8 + off_tbox);
-    g.amask = reinterpret_cast<unsigned long long*>(b8 + off_amask);
+    c->ubox = reinterpret_cast<float4*>(b8 + off_ubox);
+    c->tbox = reinterpret_cast<float4*>(b8 + off_tbox);
+    c->amask = reinterpret_cast<unsigned long long*>(b8 + off_amask);
+    g.amask = c->amask;
     g.awords = awords;
     g.cen_sp = ga->cen_sp;
     g.thr2_sp = ga->thr2_sp;
     g.sp_s = ga->sp_s;
     g.cap = cap;
-
-    cudaError_t e = cudaSuccess;
-    CUtensorMap ta, tb;
-    if (!culled && (!make_tmap(&ta, g.a, n_pad, fmt, sh.ke, 128) ||
-                    !make_tmap(&tb, bop, cols_pad, fmt, sh.ke, sh.N))) {
+    c->sh = sh;
+    c->n = n;
+    c->n_pad = n_pad;
+    c->n_units = n_units;
+    c->cols = cols;
+    c->n_tiles = cols_pad / sh.N;
+    c->n_chunks = n_chunks;
+    c->awords = awords;
+    if (!culled && (!make_tmap(&c->ta, g.a, n_pad, fmt, sh.ke, 128) ||
+                    !make_tmap(&c->tb, bop, cols_pad, fmt, sh.ke, sh.N))) {
         scratch_release(scratch, st);
         return fail(SEG_ERR_CUDA, "seg_label: cuTensorMapEncodeTiled failed");
     }
-    if (!e) e = cudaMemsetAsync(g.cnt, 0, 256, st);
+    return SEG_OK;
+}
+
+// The call's kernels on `st` (no host synchronisation, no allocation: capturable in a graph).
+// dbg_bits: the screen's survivors instead of labels (seg_gemm_screen_bits).
+cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, FiberSrc src,
+                         int* labels, float* dist, int* cidx, unsigned char* orient,
+                         cudaStream_t st, Profiler* prof, unsigned* dbg_bits, long long dbg_words) {
+    const GemmScratch& g = c.g;
+    const long long n = c.n;
+    const int sms = c.sms;
+    cudaError_t e = cudaMemsetAsync(g.cnt, 0, 256, st);
     if (!e) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_SORT, st);
         const unsigned nb = (unsigned)((n + 255) / 256);
-        e = cudaMemsetAsync(hist, 0, (size_t)NBINS * 4, st);
-        if (!e) k_bin_count<<<nb, 256, 0, st>>>(fib, n, at, bin, hist);
-        if (!e) k_bin_scan<<<NTOP, SCAN_BLOCK, 0, st>>>(hist, top);
-        if (!e) k_bin_scan_top<<<1, 32, 0, st>>>(top);
-        if (!e) k_bin_scatter<<<nb, 256, 0, st>>>(bin, n, hist, top, perm);
+        e = cudaMemsetAsync(c.hist, 0, (size_t)NBINS * 4, st);
+        if (!e) k_bin_count<<<nb, 256, 0, st>>>(src, n, at, c.bin, c.hist);
+        if (!e) k_bin_scan<<<NTOP, SCAN_BLOCK, 0, st>>>(c.hist, c.top);
+        if (!e) k_bin_scan_top<<<1, 32, 0, st>>>(c.top);
+        if (!e) k_bin_scatter<<<nb, 256, 0, st>>>(c.bin, n, c.hist, c.top, c.perm);
         if (!e) e = cudaGetLastError();
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_PREP, st);
         const long long rows_per_block = 32LL * PREP_WARPS;
-        const unsigned pb = (unsigned)((n_pad + rows_per_block - 1) / rows_per_block);
-        auto prep = culled ? k_prep_a<0, false>
-                    : tf32 ? (inv ? k_prep_a<2, true> : k_prep_a<2, false>)
-                           : (inv ? k_prep_a<1, true> : k_prep_a<1, false>);
-        prep<<<pb, PREP_WARPS * 32, 0, st>>>(fib, perm, n, n_pad, at, g.a, g.alpha, g.key, g.fs,
-                                             ubox);
+        const unsigned pb = (unsigned)((c.n_pad + rows_per_block - 1) / rows_per_block);
+        auto prep = c.culled ? k_prep_a<0, false>
+                    : c.tf32 ? (c.inv ? k_prep_a<2, true> : k_prep_a<2, false>)
+                             : (c.inv ? k_prep_a<1, true> : k_prep_a<1, false>);
+        prep<<<pb, PREP_WARPS * 32, 0, st>>>(src, c.perm, n, c.n_pad, at, g.a, g.alpha, g.key,
+                                             g.fs, c.ubox);
         // centroids per 32-column chunk: 32 (orientation-free) or 16 (directional)
-        if (!e) e = cudaGetLastError();
-        if (!e)
-            k_tile_box<<<(n_chunks + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M, inv ? 32 : 16,
-                                                              n_chunks, tbox);
-        if (!e && !culled)
-            k_block_mask<<<(unsigned)((n_units + 3) / 4), 128, 0, st>>>(
-                ubox, tbox, n_units, sh.R, n_chunks, awords,
-                reinterpret_cast<unsigned long long*>(b8 + off_amask));
         e = cudaGetLastError();
+        if (!e)
+            k_tile_box<<<(c.n_chunks + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M,
+                                                                c.inv ? 32 : 16, c.n_chunks,
+                                                                c.tbox);
+        if (!e && !c.culled)
+            k_block_mask<<<(unsigned)((c.n_units + 3) / 4), 128, 0, st>>>(
+                c.ubox, c.tbox, c.n_units, c.sh.R, c.n_chunks, c.awords, c.amask);
+        if (!e) e = cudaGetLastError();
     }
     if (!e) {
-        ProfScope ps(prof, culled ? PROF_CULL_SCREEN : PROF_GEMM_SCREEN, st);
-        if (culled) {
-            const long long n_groups = n_pad / 32;
+        ProfScope ps(prof, c.culled ? PROF_CULL_SCREEN : PROF_GEMM_SCREEN, st);
+        if (c.culled) {
+            const long long n_groups = c.n_pad / 32;
             k_culled_screen<<<(unsigned)std::min<long long>((n_groups + CS_WARPS - 1) / CS_WARPS,
                                                             (long long)sms * 8),
-                              CS_WARPS * 32, 0, st>>>(n, n_groups, at, g, ga->scr_sp, ubox, tbox,
-                                                      n_chunks);
+                              CS_WARPS * 32, 0, st>>>(n, n_groups, at, g, ga->scr_sp, c.ubox,
+                                                      c.tbox, c.n_chunks);
             e = cudaGetLastError();
         } else {
-            e = dispatch_screen(sh, ta, tb, n_units, n_tiles, cols, g, at.status, sms, st);
+            e = dispatch_screen(c.sh, c.ta, c.tb, c.n_units, c.n_tiles, c.cols, g, at.status, sms,
+                                st);
         }
     }
     if (!e && dbg_bits) {  // diagnostic: the screen's survivors instead of labels
         e = cudaMemsetAsync(dbg_bits, 0, (size_t)n * dbg_words * 4, st);
         if (!e)
-            k_survivor_bits<<<sms * 8, 256, 0, st>>>(n, at, g, inv ? 1 : 0, dbg_bits, dbg_words,
-                                                     n * (long long)cols, ga->stats);
+            k_survivor_bits<<<sms * 8, 256, 0, st>>>(n, at, g, c.inv ? 1 : 0, dbg_bits, dbg_words,
+                                                     n * (long long)c.cols, ga->stats);
         if (!e) e = cudaGetLastError();
-        seg_status r = scratch_release(scratch, st);
-        if (e) return cuda_fail(e, "seg_gemm_screen_bits");
-        return r;
+        return e;
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
-        if (inv)
+        if (c.inv)
             k_exact_blocks<true><<<sms * 8, EX_THREADS, 0, st>>>(at, g);
         else
             k_exact_blocks<false><<<sms * 9, EX_THREADS, 0, st>>>(at, g);
@@ -1654,11 +1690,77 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
         ProfScope ps(prof, PROF_GEMM_FINAL, st);
         k_overflow_rescan<<<sms * 4, 256, 0, st>>>(n, at, g);
         k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-            n, at, g, labels, dist, cidx, orient, n * (long long)cols, ga->stats);
+            n, at, g, src, labels, dist, cidx, orient, n * (long long)c.cols, ga->stats);
         e = cudaGetLastError();
     }
-    seg_status r = scratch_release(scratch, st);
-    if (e) return cuda_fail(e, "seg_label: GEMM mode");
+    return e;
+}
+
+seg_status label_gemm(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, std::mutex* mu,
+                      const float* fib, long long n, int mode, int* labels, float* dist,
+                      int* cidx, unsigned char* orient, cudaStream_t st, int config,
+                      Profiler* prof, unsigned* dbg_bits, long long dbg_words) {
+    std::lock_guard<std::mutex> lock(*mu);
+    GemmCall c;
+    seg_status s = gemm_setup(at, ga, scratch, n, mode, config, st, &c);
+    if (s != SEG_OK) return s;
+    const FiberSrc src{fib, nullptr, 0};
+    const cudaError_t e = gemm_enqueue(c, at, ga, src, labels, dist, cidx, orient, st, prof,
+                                       dbg_bits, dbg_words);
+    const seg_status r = scratch_release(scratch, st);
+    if (e) return cuda_fail(e, dbg_bits ? "seg_gemm_screen_bits" : "seg_label: GEMM mode");
+    return r;
+}
+
+// seg_label_batch in the GEMM modes: the subjects are one virtual array of `total` fibers
+// (FiberSrc over the device work table), sorted and screened together, and the whole sequence
+// of kernels is captured once into a CUDA graph per (mode, tile shape, subject count, total,
+// scratch buffer) and replayed. Stream order on `st`: the scratch's previous user, then the
+// table upload (from the pinned host table; `copied_event` is recorded after it), then the
+// graph. The caller holds the atlas mutex.
+seg_status gemm_batch_launch(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
+                             BatchState* b, int nsubj, long long total, int mode, int config,
+                             const void* host_table, size_t table_bytes, void* copied_event,
+                             cudaStream_t st) {
+    GemmCall c;
+    seg_status s = gemm_setup(at, ga, scratch, total, mode, config, st, &c);
+    if (s != SEG_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (!b->graph_exec || b->mode != mode || b->config != config || b->nsubj != nsubj ||
+        b->total != total || b->scratch_ptr != c.g.a) {
+        if (b->graph_exec) {
+            cudaGraphExecDestroy((cudaGraphExec_t)b->graph_exec);
+            b->graph_exec = nullptr;
+        }
+        cudaStream_t cs = (cudaStream_t)b->cap_stream;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (!e) {
+            const FiberSrc src{nullptr, (const BatchEntry*)b->table, nsubj};
+            const cudaError_t e1 = gemm_enqueue(c, at, ga, src, nullptr, nullptr, nullptr, nullptr,
+                                                cs, nullptr, nullptr, 0);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (!e) e = e1;
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (!e) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e) {
+            scratch_release(scratch, st);
+            return cuda_fail(e, "seg_label_batch: capture of the GEMM-mode sequence");
+        }
+        b->graph_exec = exec;
+        b->mode = mode;
+        b->config = config;
+        b->nsubj = nsubj;
+        b->total = total;
+        b->scratch_ptr = c.g.a;
+    }
+    e = cudaMemcpyAsync(b->table, host_table, table_bytes, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaEventRecord((cudaEvent_t)copied_event, st);
+    if (!e) e = cudaGraphLaunch((cudaGraphExec_t)b->graph_exec, st);
+    const seg_status r = scratch_release(scratch, st);
+    if (e) return cuda_fail(e, "seg_label_batch: graph launch");
     return r;
 }
 

@@ -80,8 +80,31 @@ struct BatchEntry {
     long long n;
     int* labels;
     float* dist;
-    long long tile0;  // first work item (32-fiber tile) of this subject
-    long long pad;
+    long long tile0;  // first work item (32-fiber tile) of this subject (plain mode)
+    long long first;  // its first fiber in the concatenation of all subjects (GEMM modes)
+};
+
+// Where the GEMM modes read fibers and write results: one subject (fib, outputs given to the
+// kernel), or several subjects concatenated into one virtual array of fibers, index i being
+// fiber i - table[k].first of subject k = the last entry with table[k].first <= i (entry
+// nsubj holds first = the total, so empty subjects are never chosen for a valid i).
+struct FiberSrc {
+    const float* fib;
+    const BatchEntry* table;
+    int nsubj;
+    __device__ __forceinline__ int subject(long long i) const {
+        int lo = 0, hi = nsubj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid].first <= i) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ const float* row(long long i) const {
+        if (!table) return fib + (size_t)i * (3 * SEG_NPTS);
+        const int k = subject(i);
+        return table[k].fib + (size_t)(i - table[k].first) * (3 * SEG_NPTS);
+    }
 };
 
 // Plain exact labelling of n fibers (SEG_MODE_PLAIN).

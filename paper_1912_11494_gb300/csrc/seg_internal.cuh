@@ -87,16 +87,21 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, 
                       Profiler* prof = nullptr, unsigned* dbg_bits = nullptr,
                       long long dbg_words = 0);
 
-// Cached CUDA graph of the batched launch: counter reset, work-table upload (from a pinned
-// host copy the host rewrites before each replay) and the persistent kernel.
+// Cached CUDA graph of the batched launch. The work table goes to the device with one copy on
+// the caller's stream before each replay, from one of two pinned host buffers used by
+// alternate calls (a buffer is rewritten only after the copy of two calls ago has run), so
+// back-to-back calls do not wait for each other on the host.
 struct BatchState {
     void* graph_exec = nullptr;   // cudaGraphExec_t
-    int nsubj = -1;
-    int config = -1;
-    void* table = nullptr;        // device BatchEntry[nsubj + 1]
-    void* table_host = nullptr;   // pinned host copy
+    int mode = -1, nsubj = -1, config = -1;
+    long long total = -1;         // fibers of all subjects (GEMM modes: sizes the graph)
+    void* scratch_ptr = nullptr;  // the scratch the GEMM graph was captured on
+    void* table = nullptr;        // device BatchEntry[table_cap]
+    void* table_host[2] = {nullptr, nullptr};  // pinned copies
+    void* copied[2] = {nullptr, nullptr};      // cudaEvent_t after each buffer's last copy
+    int next = 0;                 // host buffer of the next call
     size_t table_cap = 0;         // entries allocated
-    void* counter = nullptr;      // device work counter
+    void* counter = nullptr;      // device work counter (plain mode)
     void* cap_stream = nullptr;   // cudaStream_t used for capture
     void* done = nullptr;         // cudaEvent_t recorded after each replay
 };
@@ -105,6 +110,12 @@ seg_status batch_launch(const AtlasView& at, GemmAtlas* g, BatchState* b, Scratc
                         std::mutex* mu, int nsubj, const float* const* fib,
                         const long long* counts, int mode, int* const* labels,
                         float* const* dist, cudaStream_t st, int config);
+// GEMM modes: every subject in one virtual array through one captured launch sequence (table
+// already uploaded to b->table by the caller's stream order, see batch_launch).
+seg_status gemm_batch_launch(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
+                             BatchState* b, int nsubj, long long total, int mode, int config,
+                             const void* host_table, size_t table_bytes, void* copied_event,
+                             cudaStream_t st);
 
 seg_status grad_launch(const AtlasView& at, const int* inv_perm, ScratchArena* scratch,
                        std::mutex* mu, const float* fib, long long n, const double* h_aff,

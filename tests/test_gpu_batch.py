@@ -1,10 +1,12 @@
-"""GPU tests of seg_label_batch: many subjects of uneven size in one persistent launch (a CUDA
-graph captured once per subject count and replayed with a new work table)."""
+"""GPU tests of seg_label_batch: many subjects of uneven size in one captured launch sequence
+(a CUDA graph captured once per batch shape and replayed with a new work table, copied from
+one of two pinned host buffers used by alternate calls)."""
 import numpy as np
 import pytest
 import torch
 
 from paper_1912_11494_gb300 import binding, synth
+import oracle
 from tests import parity
 
 pytestmark = pytest.mark.gpu
@@ -87,3 +89,69 @@ def test_every_tile_shape_in_batch(env):
             np.testing.assert_array_equal(l, rl)
             np.testing.assert_array_equal(d, rd)
     binding.seg_set_config(at, "plain", 0)
+
+
+@pytest.mark.parametrize("mode", ["gemm_bf16", "plain_culled", "gemm_inv_tf32"])
+def test_graph_replay_recapture_and_back_to_back(env, mode):
+    """GEMM and culled modes: replays with the same shape, recaptures when the total or the
+    subject count changes, and back-to-back calls with no synchronisation in between (the two
+    pinned tables alternate)."""
+    dev, a, at = env
+    sets = [subjects(a, c, seed * 100, dev) for c, seed in
+            (([500, 2000, 17], 7), ([500, 2000, 17], 8), ([3000, 5, 999, 0], 9), ([1200], 10))]
+    outs = []
+    for fibs in sets:  # no synchronisation between the calls
+        labs = [torch.full((f.shape[0],), -7, dtype=torch.int32, device=dev) for f in fibs]
+        dists = [torch.full((f.shape[0],), -7.0, device=dev) for f in fibs]
+        binding.seg_label_batch(at, fibs, mode, labs, dists)
+        outs.append((labs, dists))
+    binding.seg_sync_status(at)
+    for fibs, (labs, dists) in zip(sets, outs):
+        for f, l, d in zip(fibs, labs, dists):
+            rl, rd = single(at, f, "plain")
+            np.testing.assert_array_equal(l.cpu().numpy(), rl)
+            np.testing.assert_array_equal(d.cpu().numpy(), rd)
+
+
+@pytest.fixture(scope="module")
+def c4(env):
+    """The 16-subject batch: counts log-uniform in [0.3M, 4.2M] (seeds 0-15, 28.6M fibers in
+    all) against the 500-bundle x 20-centroid atlas."""
+    dev = env[0]
+    atlas = synth.make_atlas(500, seed=1002, device=dev)
+    fibs = [torch.as_tensor(synth.make_batch_subject(atlas, s, device=dev), device=dev)
+            for s in range(16)]
+    at = binding.Atlas(torch.as_tensor(atlas.centroids, device=dev),
+                       torch.as_tensor(atlas.bundle_of, device=dev),
+                       torch.as_tensor(atlas.thresholds, device=dev))
+    return atlas, at, fibs
+
+
+@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "plain_culled"])
+def test_full_size_batch(env, c4, mode):
+    """The full 16-subject batch in one call: every fiber of every subject equal to a single
+    seg_label call on that subject (whose full-size parity is checked fiber by fiber in
+    test_gpu_label.py), and 20,000 random fibers per subject against the oracle."""
+    dev = env[0]
+    atlas, at, fibs = c4
+    assert 28_000_000 < sum(int(f.shape[0]) for f in fibs) < 29_500_000
+    labs = [torch.full((f.shape[0],), -7, dtype=torch.int32, device=dev) for f in fibs]
+    dists = [torch.full((f.shape[0],), -7.0, device=dev) for f in fibs]
+    binding.seg_label_batch(at, fibs, mode, labs, dists)
+    binding.seg_sync_status(at)
+    rng = np.random.default_rng(4)
+    ties = 0
+    for s, f in enumerate(fibs):
+        lab = labs[s].cpu().numpy()
+        dst = dists[s].cpu().numpy()
+        rl, rd, _, _ = binding.label(at, f, "plain")
+        binding.seg_sync_status(at)
+        np.testing.assert_array_equal(lab, rl.cpu().numpy())
+        np.testing.assert_array_equal(dst, rd.cpu().numpy())
+        idx = np.sort(rng.choice(f.shape[0], size=20_000, replace=False))
+        fn = f[torch.as_tensor(idx, device=dev)].cpu().numpy()
+        res = parity.compare_all(fn, atlas.centroids, atlas.bundle_of, atlas.thresholds,
+                                 lab[idx], dst[idx])
+        ties += res["near_ties"]
+    print(f"\n{mode}: 16 subjects equal to single calls; 320,000 sampled fibers against the "
+          f"oracle, {ties} near-ties")
