@@ -52,10 +52,16 @@ def _bind(lib):
                                     ctypes.c_int]
     lib.oracle_near_tie_pruned.argtypes = lib.oracle_near_tie.argtypes
     lib.oracle_dme_pairs.argtypes = [P, I64, P, I64, P, P, P, P, ctypes.c_int]
+    lib.oracle_label_cls.argtypes = [P, I64, P, P, I64, P, I32, ctypes.c_int, P, P, P, P,
+                                     ctypes.c_int]
+    lib.oracle_near_tie_cls.argtypes = [P, I64, P, P, I64, P, I32, ctypes.c_int, P, P,
+                                        ctypes.c_double, P, ctypes.c_int]
+    lib.oracle_lengths.argtypes = [P, I64, P]
     lib.oracle_grad.argtypes = [P, I64, P, P, P, I64, P, I32, P, P, P, P, P, P, P, P, P, P, P,
                                 ctypes.c_int]
     for f in (lib.oracle_dme_matrix, lib.oracle_label_brute, lib.oracle_label_cascade,
               lib.oracle_near_tie, lib.oracle_near_tie_pruned, lib.oracle_dme_pairs,
+              lib.oracle_label_cls, lib.oracle_near_tie_cls, lib.oracle_lengths,
               lib.oracle_grad):
         f.restype = ctypes.c_int
     return lib
@@ -157,6 +163,59 @@ def near_tie(fibers, centroids, bundle_of, thresholds, labels, dist, tol: float 
     _check(fn(_ptr(fib), n, _ptr(cen), _ptr(bo), cen.shape[0], _ptr(thr), thr.shape[0],
               _ptr(lab), _ptr(dist), tol, _ptr(flag), nthreads))
     return flag
+
+
+CLASSIFICATIONS = {"eq2": 0, "eq2_tn": 1, "paper": 2}
+
+
+def label_cls(fibers, centroids, bundle_of, thresholds, cls: str, nthreads: int = 0):
+    """Labelling with the length term TN of Eq. 3 (lazy, Section 2.4): cls "eq2_tn" adds TN to
+    Eq. 2's d_ME; cls "paper" is the paper's new algorithm (direction inferred from test2's end
+    points, tests 3-4 in that orientation only, then TN). dict of labels, dist (= D, the
+    classification distance), cidx, orient. cls "eq2" is label(..., "brute")."""
+    if cls == "eq2":
+        r = label(fibers, centroids, bundle_of, thresholds, "brute", nthreads)
+        return {k: r[k] for k in ("labels", "dist", "cidx", "orient")}
+    fib = _f32(fibers).reshape(-1, 63)
+    cen = _f32(centroids).reshape(-1, 63)
+    bo = np.ascontiguousarray(bundle_of, dtype=np.int32)
+    thr = _f32(thresholds)
+    n = fib.shape[0]
+    out = dict(labels=np.empty(n, np.int32), dist=np.empty(n), cidx=np.empty(n, np.int32),
+               orient=np.empty(n, np.uint8))
+    _check(_load().oracle_label_cls(_ptr(fib), n, _ptr(cen), _ptr(bo), cen.shape[0], _ptr(thr),
+                                    thr.shape[0], CLASSIFICATIONS[cls], _ptr(out["labels"]),
+                                    _ptr(out["dist"]), _ptr(out["cidx"]), _ptr(out["orient"]),
+                                    nthreads))
+    return out
+
+
+def near_tie_cls(fibers, centroids, bundle_of, thresholds, cls: str, labels, dist,
+                 tol: float = 2e-3, nthreads: int = 0):
+    """uint8 [n]: 1 where label_cls's result is not decidable at tolerance tol (mm)."""
+    if cls == "eq2":
+        return near_tie(fibers, centroids, bundle_of, thresholds, labels, dist, tol, nthreads,
+                        pruned=True)
+    fib = _f32(fibers).reshape(-1, 63)
+    cen = _f32(centroids).reshape(-1, 63)
+    bo = np.ascontiguousarray(bundle_of, dtype=np.int32)
+    thr = _f32(thresholds)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    dist = np.ascontiguousarray(dist, dtype=np.float64)
+    n = fib.shape[0]
+    flag = np.empty(n, np.uint8)
+    _check(_load().oracle_near_tie_cls(_ptr(fib), n, _ptr(cen), _ptr(bo), cen.shape[0],
+                                       _ptr(thr), thr.shape[0], CLASSIFICATIONS[cls], _ptr(lab),
+                                       _ptr(dist), tol, _ptr(flag), nthreads))
+    return flag
+
+
+def lengths(fibers):
+    """Polyline arc length of each 21-point fiber, float64 [n]."""
+    fib = _f32(fibers).reshape(-1, 63)
+    out = np.empty(fib.shape[0])
+    _check(_load().oracle_lengths(_ptr(fib), fib.shape[0], _ptr(out)))
+    return out
 
 
 def grad(fibers, affine12, centroids, bundle_of, thresholds, mask=None, frozen=None,

@@ -465,6 +465,199 @@ int oracle_dme_pairs(const float *fib, int64_t n, const float *cen, int64_t M,
     return 0;
 }
 
+/* ---- paper-faithful classification (Section 2.3 Eq. 3, Section 2.4) ------------------------ */
+
+/* Arc length of a 21-point polyline: the sum of its 20 segment lengths (Eq. 1 between
+ * consecutive points). Read as the fiber length l_S / centroid length l_C of Eq. 3. */
+static double poly_length(const double *a) {
+    double l = 0.0;
+    for (int i = 0; i + 1 < NPTS; ++i) l += d_E(a + 3 * i, a + 3 * (i + 1));
+    return l;
+}
+
+/* Eq. 3: TN = (|l_S - l_C| / max(l_S, l_C) + 1)^2 - 1; two zero lengths give 0. */
+static double tn_term(double ls, double lc) {
+    double m = ls > lc ? ls : lc;
+    if (!(m > 0.0)) return 0.0;
+    double r = fabs(ls - lc) / m;
+    return (r + 1.0) * (r + 1.0) - 1.0;
+}
+
+/* Classification distance of one pair, or +inf when the pair is discarded.
+ * cls 1 (Eq. 2 + TN, lazy): d = min(dd, dr) of Eq. 2; a pair with d > theta is discarded
+ *   before TN is computed (Section 2.4, the new algorithm's last optimization); else
+ *   D = d + TN, and the pair passes when D <= theta.
+ * cls 2 (the paper's new algorithm, Section 2.4): test1 on the centre point; test2 computes both
+ *   orientations' end-point distances and infers the direction as the orientation with the
+ *   smaller partial maximum (ties: direct); test3 and test4 then run in that orientation only,
+ *   each distance checked against theta at once; D = that orientation's maximum + TN (lazy). */
+static double cls_distance(int cls, const double *a, const double *b, double th, double ls,
+                           double lc, int *orient) {
+    if (cls == 1) {
+        double dd, dr;
+        dme_both(a, b, &dd, &dr);
+        double d = dd <= dr ? dd : dr;
+        *orient = dd <= dr ? 0 : 1;
+        if (d > th) return INFINITY;
+        return d + tn_term(ls, lc);
+    }
+    double m = d_E(a + 3 * CENTRE, b + 3 * CENTRE); /* test1 */
+    if (m > th) return INFINITY;
+    double ed = m, er = m; /* test2, both orientations */
+    double x;
+    x = d_E(a, b);                                  if (x > ed) ed = x;
+    x = d_E(a + 3 * (NPTS - 1), b + 3 * (NPTS - 1)); if (x > ed) ed = x;
+    x = d_E(a, b + 3 * (NPTS - 1));                 if (x > er) er = x;
+    x = d_E(a + 3 * (NPTS - 1), b);                 if (x > er) er = x;
+    if (ed > th && er > th) return INFINITY;
+    int o = ed <= er ? 0 : 1; /* direction inference */
+    *orient = o;
+    m = o ? er : ed;
+    for (int q = 0; q < 4; ++q) { /* test3 */
+        x = d_E(a + 3 * TEST3[q], b + 3 * (o ? rev(TEST3[q]) : TEST3[q]));
+        if (x > th) return INFINITY;
+        if (x > m) m = x;
+    }
+    for (int i = 1; i < NPTS - 1; ++i) { /* test4 */
+        if (i == CENTRE || i == 5 || i == 15 || i == 3 || i == 17) continue;
+        x = d_E(a + 3 * i, b + 3 * (o ? rev(i) : i));
+        if (x > th) return INFINITY;
+        if (x > m) m = x;
+    }
+    if (m > th) return INFINITY;
+    return m + tn_term(ls, lc); /* lazy TN: only for a pair that got this far */
+}
+
+/* Labelling with classification cls (1 or 2, see cls_distance): a pair passes when D <= theta;
+ * the fiber takes the bundle of the passing centroid with the smallest D, visiting bundles in
+ * increasing index and replacing the best only on a strict decrease (Algorithm 1). dist = D. */
+int oracle_label_cls(const float *fib, int64_t n, const float *cen, const int32_t *bundle_of,
+                     int64_t M, const float *thr, int32_t B, int cls, int32_t *labels,
+                     double *dist, int32_t *cidx, uint8_t *orient, int nthreads) {
+    if (cls != 1 && cls != 2) return 2;
+    int64_t *ord = bundle_order(bundle_of, M, B);
+    double *C = malloc((size_t)(M > 0 ? M : 1) * NC * sizeof(double));
+    double *L = malloc((size_t)(M > 0 ? M : 1) * sizeof(double));
+    if (!ord || !C || !L) {
+        free(ord);
+        free(C);
+        free(L);
+        return 1;
+    }
+    promote(cen, C, M * NC);
+    for (int64_t c = 0; c < M; ++c) L[c] = poly_length(C + c * NC);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t f = 0; f < n; ++f) {
+        double a[NC];
+        promote(fib + f * NC, a, NC);
+        result_t r;
+        result_none(&r);
+        if (!all_finite(a)) {
+            r.dist = NAN;
+        } else {
+            double ls = poly_length(a);
+            for (int64_t k = 0; k < M; ++k) {
+                int64_t c = ord[k];
+                double th = (double)thr[bundle_of[c]];
+                int o = 0;
+                double D = cls_distance(cls, a, C + c * NC, th, ls, L[c], &o);
+                if (D <= th && D < r.dist) {
+                    r.dist = D;
+                    r.label = bundle_of[c];
+                    r.cidx = c;
+                    r.orient = o;
+                }
+            }
+        }
+        if (labels) labels[f] = r.label;
+        if (dist) dist[f] = r.dist;
+        if (cidx) cidx[f] = (int32_t)r.cidx;
+        if (orient) orient[f] = (uint8_t)r.orient;
+    }
+    free(ord);
+    free(C);
+    free(L);
+    return 0;
+}
+
+/* Decidability of oracle_label_cls's result at tolerance tol (mm), on the classification
+ * distance D. A pair's candidate values: D itself (cls 1; D = min(dd, dr) + TN); for cls 2 the
+ * value D_o = max_o + TN of every orientation o whose test2 maximum is within tol of the smaller
+ * one (an FP32 implementation may infer either). flag[f] = 1 when (i) a candidate within tol of
+ * the best D (any, if unlabelled) lies within tol of its threshold, (ii) a candidate of another
+ * bundle passes its threshold + tol within tol of the best D, or (iii) (cls 2) a centroid with
+ * two possible orientations has a candidate that passes its threshold + tol within tol of the
+ * best D or below it. Candidates whose centre-point distance exceeds theta + tol are skipped. */
+int oracle_near_tie_cls(const float *fib, int64_t n, const float *cen, const int32_t *bundle_of,
+                        int64_t M, const float *thr, int32_t B, int cls, const int32_t *labels,
+                        const double *dist, double tol, uint8_t *flag, int nthreads) {
+    (void)B;
+    double *C = malloc((size_t)(M > 0 ? M : 1) * NC * sizeof(double));
+    double *L = malloc((size_t)(M > 0 ? M : 1) * sizeof(double));
+    if (!C || !L) {
+        free(C);
+        free(L);
+        return 1;
+    }
+    promote(cen, C, M * NC);
+    for (int64_t c = 0; c < M; ++c) L[c] = poly_length(C + c * NC);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t f = 0; f < n; ++f) {
+        double a[NC];
+        promote(fib + f * NC, a, NC);
+        uint8_t fl = 0;
+        if (all_finite(a)) {
+            const double Db = dist[f], ls = poly_length(a);
+            const int unl = labels[f] < 0;
+            for (int64_t c = 0; c < M && !fl; ++c) {
+                const double *b = C + c * NC;
+                const double th = (double)thr[bundle_of[c]];
+                if (d_E(a + 3 * CENTRE, b + 3 * CENTRE) > th + tol) continue;
+                double dd, dr;
+                dme_both(a, b, &dd, &dr);
+                const double tn = tn_term(ls, L[c]);
+                double cand[2];
+                int nc = 0;
+                if (cls == 1) {
+                    cand[nc++] = (dd <= dr ? dd : dr) + tn;
+                } else {
+                    double m = d_E(a + 3 * CENTRE, b + 3 * CENTRE), ed = m, er = m, x;
+                    x = d_E(a, b);                                  if (x > ed) ed = x;
+                    x = d_E(a + 3 * (NPTS - 1), b + 3 * (NPTS - 1)); if (x > ed) ed = x;
+                    x = d_E(a, b + 3 * (NPTS - 1));                 if (x > er) er = x;
+                    x = d_E(a + 3 * (NPTS - 1), b);                 if (x > er) er = x;
+                    const double lo = ed <= er ? ed : er;
+                    if (ed <= lo + tol) cand[nc++] = dd + tn;
+                    if (er <= lo + tol) cand[nc++] = dr + tn;
+                }
+                for (int k = 0; k < nc && !fl; ++k) {
+                    const double D = cand[k];
+                    if (D > th + tol) continue;
+                    if ((unl || D <= Db + tol) && fabs(D - th) <= tol) fl = 1;
+                    if (bundle_of[c] != labels[f] && fabs(D - Db) <= tol) fl = 1;
+                    if (nc == 2 && (unl || D <= Db + tol)) fl = 1;
+                }
+            }
+        }
+        flag[f] = fl;
+    }
+    free(C);
+    free(L);
+    return 0;
+}
+
+/* Fiber polyline lengths (for tests of Eq. 3's l_S). */
+int oracle_lengths(const float *fib, int64_t n, double *len) {
+    for (int64_t f = 0; f < n; ++f) {
+        double a[NC];
+        promote(fib + f * NC, a, NC);
+        len[f] = poly_length(a);
+    }
+    return 0;
+}
+
 /* y = M x + t for every point, in double. aff = M row-major (9) then t (3). */
 static void apply_affine(const double *aff, const double *x, double *y) {
     for (int p = 0; p < NPTS; ++p) {

@@ -1,7 +1,8 @@
 """Plants plausible mistakes in a copy of the oracle (CPU only) and checks that the pins in
 test_oracle_pins.py catch every one of them: a wrong reversal index, a dropped or sign-flipped
 coordinate term, a strict threshold, a non-strict update, min/max swaps, a lost bundle visit
-order, and gradient slips."""
+order, gradient slips, and slips in the length term TN (Eq. 3), the polyline length and the
+direction inference of Section 2.4."""
 import ctypes
 import os
 import subprocess
@@ -32,6 +33,19 @@ MUTANTS = {
     "grad_uses_moved_point": ("g[3 * r + c] += u[r] * x[3 * is + c];",
                               "g[3 * r + c] += u[r] * y[3 * is + c];"),
     "grad_centroid_index": ("int pi = o ? rev(is) : is;", "int pi = is;"),
+    "tn_signed_difference": ("double r = fabs(ls - lc) / m;", "double r = (ls - lc) / m;"),
+    "tn_squared_ratio": ("return (r + 1.0) * (r + 1.0) - 1.0;", "return r * r;"),
+    "length_drops_a_segment": ("for (int i = 0; i + 1 < NPTS; ++i) l += d_E",
+                               "for (int i = 1; i + 1 < NPTS; ++i) l += d_E"),
+    "inference_takes_larger": ("int o = ed <= er ? 0 : 1; /* direction inference */",
+                               "int o = ed <= er ? 1 : 0; /* direction inference */"),
+    "inference_skipped": ("    m = o ? er : ed;\n    for (int q = 0; q < 4; ++q) { /* test3 */",
+                          "    m = o ? er : ed;\n    if (0) { double dd, dr; dme_both(a, b, &dd, &dr);"
+                          " return (dd <= dr ? dd : dr) + tn_term(ls, lc); }\n"
+                          "    if (1) { double dd, dr; dme_both(a, b, &dd, &dr);"
+                          " if ((dd <= dr ? dd : dr) > th) return INFINITY;"
+                          " *orient = dd <= dr ? 0 : 1; return (dd <= dr ? dd : dr) + tn_term(ls, lc); }\n"
+                          "    for (int q = 0; q < 4; ++q) { /* test3 */"),
 }
 
 PINS = [pins.test_worked_examples_dme, pins.test_worked_examples_labels,
@@ -39,7 +53,9 @@ PINS = [pins.test_worked_examples_dme, pins.test_worked_examples_labels,
         pins.test_identities, pins.test_labels_vs_sorted_brute_force,
         pins.test_exact_ties_and_threshold_edges, pins.test_grad_translation_closed_form,
         pins.test_grad_reversed_orientation_closed_form,
-        pins.test_grad_frozen_structure_fd]
+        pins.test_grad_frozen_structure_fd, pins.test_lengths_closed_forms,
+        pins.test_tn_worked_example,
+        pins.test_direction_inference_can_miss_the_closer_orientation]
 
 
 def _gold():

@@ -308,6 +308,98 @@ def test_dme_pairs_equals_matrix_diagonal():
     assert np.isnan(p[3]) and np.isfinite(np.delete(p, 3)).all()
 
 
+def _line(step, n=21):
+    t = np.arange(n, dtype=np.float64)
+    return np.stack([step * t, 0 * t, 0 * t], axis=1)
+
+
+def test_lengths_closed_forms():
+    """Eq. 3's fiber and centroid lengths, read as the arc length of the 21-point polyline: a
+    straight fiber with spacing s has length 20 s; 21 points on a circle of radius R at equal
+    angle steps phi have length 20 * 2 R sin(phi / 2)."""
+    R, phi = 7.0, 0.1
+    t = np.arange(21)
+    circ = np.stack([R * np.cos(phi * t), R * np.sin(phi * t), 0 * t], axis=1)
+    ln = oracle.lengths(np.stack([_line(1.5), circ]).astype(np.float32))
+    assert ln[0] == pytest.approx(30.0, abs=1e-12)
+    assert ln[1] == pytest.approx(20 * 2 * R * np.sin(phi / 2), rel=1e-6)
+
+
+def test_tn_worked_example():
+    """Eq. 3 on a hand-computed pair: fiber x_i = i (length 20) and centroid x_i = 1.1 i (length
+    22). The direct point distances are 0.1 i, so d_ME = 2.0 (point 20; the reversed maximum is
+    22); TN = (|20 - 22| / 22 + 1)^2 - 1 = 23/121; D = 2 + 23/121 = 2.190082... With
+    theta = 3 every classification labels the fiber (at D with TN); with theta = 2.1 Eq. 2
+    alone passes it (2.0 <= 2.1 < D). The paper's direction inference picks the direct
+    orientation here (end points 2.0 against 22)."""
+    fib = _line(1.0)[None].astype(np.float32)
+    cen = _line(1.1)[None].astype(np.float32)
+    D = 2.0 + 23.0 / 121.0
+    for th, want_tn in ((3.0, True), (2.1, False)):
+        thr = np.array([th], np.float32)
+        r = oracle.label_cls(fib, cen, [0], thr, "eq2")
+        assert r["labels"][0] == 0 and r["dist"][0] == pytest.approx(2.0, abs=1e-5)
+        for cls in ("eq2_tn", "paper"):
+            r = oracle.label_cls(fib, cen, [0], thr, cls)
+            if want_tn:
+                assert r["labels"][0] == 0 and r["dist"][0] == pytest.approx(D, abs=1e-5)
+                assert r["orient"][0] == 0
+            else:
+                assert r["labels"][0] == -1 and np.isinf(r["dist"][0])
+    # equal lengths: TN = 0 and D = d_ME (a rigid translation keeps the length)
+    r = oracle.label_cls(fib, fib + np.float32(1.5), [0], [3.0], "eq2_tn")
+    assert r["dist"][0] == pytest.approx(np.sqrt(3 * 1.5 ** 2), abs=1e-6)
+
+
+def test_direction_inference_can_miss_the_closer_orientation():
+    """Section 2.4 infers the orientation from test2's end points and runs tests 3-4 in that
+    orientation only. Fiber a: 21 points on 95% of a circle of radius 5 (end points 1.564 mm
+    apart). Centroid b: a reversed in its interior (b_j = a_(20-j), 0 < j < 20) with its end
+    points 0.5 mm above a's own (b_0 = a_0 + 0.5 z, b_20 = a_20 + 0.5 z). The end points favour
+    the direct orientation (0.5 against sqrt(1.564^2 + 0.25)), but the direct interior pairs
+    opposite sides of the loop (maximum near 10 mm), while the reversed interior matches
+    exactly, so Eq. 2's d_ME is the reversed end-point distance. Eq. 2 (with or without TN)
+    labels the fiber; the paper's algorithm discards the centroid and leaves it unlabelled."""
+    R = 5.0
+    ang = 2 * np.pi * 0.95 * np.arange(21) / 20
+    a = np.stack([R * np.cos(ang), R * np.sin(ang), 0 * ang], axis=1)
+    b = a[::-1].copy()
+    b[0] = a[0] + [0, 0, 0.5]
+    b[20] = a[20] + [0, 0, 0.5]
+    a32, b32 = a.astype(np.float32)[None], b.astype(np.float32)[None]
+    a64, b64 = a32[0].astype(np.float64), b32[0].astype(np.float64)
+    dr = max(np.linalg.norm(a64[0] - b64[20]), np.linalg.norm(a64[20] - b64[0]))
+    assert 1.6 < dr < 1.7
+    thr = np.array([3.0], np.float32)
+    r = oracle.label_cls(a32, b32, [0], thr, "eq2")
+    assert r["labels"][0] == 0 and r["orient"][0] == 1
+    assert r["dist"][0] == pytest.approx(dr, abs=1e-12)
+    r = oracle.label_cls(a32, b32, [0], thr, "eq2_tn")
+    assert r["labels"][0] == 0 and r["orient"][0] == 1 and r["dist"][0] > dr
+    r = oracle.label_cls(a32, b32, [0], thr, "paper")
+    assert r["labels"][0] == -1
+
+
+def test_near_tie_cls_flags_ambiguous_direction():
+    """A palindromic fiber (a_i = a_(20-i), a hairpin) sees the same end-point distances in
+    both orientations, so an FP32 implementation may infer either: the paper classification
+    flags it when the centroid passes; an unambiguous straight fiber is not flagged."""
+    t = np.arange(21, dtype=np.float64)
+    hair = np.stack([10 - np.abs(10 - t), 0 * t, 0 * t], axis=1)
+    cen = hair.copy()
+    cen[4] += [0, 0.8, 0]            # direct and reversed maxima differ: 0.8 against 0.8 at 16
+    cen[16] += [0, 0.3, 0]
+    fib = np.stack([hair, _line(1.0)]).astype(np.float32)
+    cens = np.stack([cen, _line(1.0) + [0, 0, 1.0]]).astype(np.float32)
+    thr = np.array([3.0, 3.0], np.float32)
+    r = oracle.label_cls(fib, cens, [0, 1], thr, "paper")
+    assert list(r["labels"]) == [0, 1]
+    flag = oracle.near_tie_cls(fib, cens, [0, 1], thr, "paper", r["labels"], r["dist"])
+    assert list(flag) == [1, 0]
+    flag = oracle.near_tie_cls(fib, cens, [0, 1], thr, "eq2_tn", r["labels"], r["dist"])
+    assert flag[1] == 0
+
+
 def test_grad_translation_closed_form():
     """One fiber, one centroid, translation only: dC/dt = u = r/|r| at the argmax point."""
     t = np.arange(21, dtype=np.float32)
