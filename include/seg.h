@@ -86,6 +86,22 @@ typedef enum {
 
 typedef struct seg_atlas seg_atlas; /* opaque; owns its device copies of the atlas */
 
+/* How a fiber is classified once its distances are known (seg_set_classification). */
+typedef enum {
+    /* d_ME of Eq. 2 (both orientations exactly), a pair passes when d_ME <= theta; the default. */
+    SEG_CLASS_EQ2 = 0,
+    /* The classification distance D = d_ME + TN (Eq. 3, TN = (|l_S - l_C| / max(l_S, l_C) +
+     * 1)^2 - 1, l the polyline arc length of the 21 points); a pair passes when D <= theta and
+     * the fiber takes the passing centroid with the smallest D. TN is computed only for pairs
+     * whose d_ME passes (Section 2.4; exact, since TN >= 0). Outputs: dist = D. */
+    SEG_CLASS_EQ2_TN = 1,
+    /* The paper's new algorithm (Section 2.4): the orientation is inferred from test2's end
+     * points (the smaller partial maximum; ties direct) and tests 3-4 run in that orientation
+     * only, then D = that orientation's maximum + TN as above. It can miss a centroid that
+     * Eq. 2 accepts in the other orientation. Outputs: dist = D, orient = the inferred one. */
+    SEG_CLASS_PAPER = 2
+} seg_classification;
+
 /* Human-readable name of a status code (static string). */
 const char* seg_status_string(seg_status s);
 
@@ -227,6 +243,15 @@ seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64
 int32_t seg_num_configs(seg_mode mode);
 seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config);
 seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config);
+
+/*
+ * Select the classification of later seg_label / seg_label_host / seg_label_batch calls on
+ * this atlas (every mode supports every classification; the default is SEG_CLASS_EQ2). The
+ * tensor-core prune and the culling stay exact: D >= d_ME >= their lower bounds. seg_grad
+ * always differentiates the Eq. 2 cost.
+ */
+seg_status seg_set_classification(seg_atlas* atlas, seg_classification cls);
+seg_status seg_get_classification(const seg_atlas* atlas, seg_classification* cls);
 
 /*
  * Kernel timing (observability; not in the paper). While enabled on an atlas, every kernel the

@@ -45,6 +45,8 @@ SIGNATURES = [
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    ("seg_set_classification", ctypes.c_int, [_P, ctypes.c_int]),
+    ("seg_get_classification", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("seg_gemm_screen_bits", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P]),
     ("seg_profile_enable", ctypes.c_int, [_P, _I32]),
     ("seg_profile_read", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64),
@@ -254,6 +256,22 @@ def seg_gemm_screen_bits(atlas: Atlas, fibers, mode, stream=None):
     _check(lib().seg_gemm_screen_bits(atlas.handle, _ptr(fib), int(fib.shape[0]), m,
                                       _ptr(bits), words, _stream(stream)))
     return bits
+
+
+CLASSIFICATIONS = {"eq2": 0, "eq2_tn": 1, "paper": 2}
+
+
+def seg_set_classification(atlas: Atlas, cls):
+    """Classification of later labelling calls: "eq2" (default), "eq2_tn" (Eq. 2 + TN) or
+    "paper" (direction inferred from the end points, + TN)."""
+    _check(lib().seg_set_classification(atlas.handle, CLASSIFICATIONS[cls] if isinstance(cls, str)
+                                        else int(cls)))
+
+
+def seg_get_classification(atlas: Atlas) -> str:
+    v = ctypes.c_int()
+    _check(lib().seg_get_classification(atlas.handle, ctypes.byref(v)))
+    return {i: k for k, i in CLASSIFICATIONS.items()}[v.value]
 
 
 def seg_sync_status(atlas: Atlas, stream=None):

@@ -336,12 +336,16 @@ k_prep_a(FiberSrc fsrc, const unsigned* __restrict__ perm, long long n,
     }
     cp_async_wait_all();
     __syncwarp();
+    // each row's length (Eq. 3's l_S, for the TN term) in its free 64th slot
+    si[lane * PREP_STRIDE + NC] = at.cls != 0 && lane < rows_in
+                                      ? poly_length(si + lane * PREP_STRIDE) : 0.0f;
+    __syncwarp();
     // the sorted copy of the rows (read by the exact re-check)
     float* fdst = fs + r0 * CROW;
 #pragma unroll 4
     for (int k = lane; k < 32 * CROW; k += 32) {
         const int r = k / CROW, c = k % CROW;
-        fdst[k] = (c < NC && r < rows_in) ? si[r * PREP_STRIDE + c] : 0.0f;
+        fdst[k] = r < rows_in ? si[r * PREP_STRIDE + c] : 0.0f;
     }
     const long long i = r0 + lane;
     float p[NC];
@@ -539,7 +543,8 @@ __global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float
     const float* src = at.cen + (size_t)s * CROW;
     for (int k = threadIdx.x; k < CROW4; k += blockDim.x)
         cen_sp[(size_t)c * CROW4 + k] =
-            k < NPTS ? make_float4(src[3 * k], src[3 * k + 1], src[3 * k + 2], 0.0f)
+            k < NPTS ? make_float4(src[3 * k], src[3 * k + 1], src[3 * k + 2],
+                                   k == 0 ? src[CROW - 1] : 0.0f)  // point 0's w: the length
                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (threadIdx.x == 0) {
         thr2_sp[c] = at.thr2[s];
@@ -1075,12 +1080,12 @@ template <bool INV>
 __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float* s_fib,
                                             const float4* s_cen, const float* s_thr,
                                             const int* s_sidx, unsigned* s_best,
-                                            unsigned long long* key, unsigned& npd) {
+                                            unsigned long long* key, unsigned& npd, int cls) {
     const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
     const int j = INV ? bit : bit >> 1;
     const float* a = s_fib + lo * FS_STRIDE;
     const float4* b = s_cen + j * CROW4;
-    const float bound = fminf(s_thr[j], __uint_as_float(s_best[lo]));
+    const float bound = fminf(s_thr[j], key_bound2(__uint_as_float(s_best[lo]), cls));
     float md = mm.x, mr = mm.y, d2;
     int o;
     bool pass;
@@ -1100,9 +1105,11 @@ __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float
         if (pass) { md = o ? rest17<1>(a, b, md) : rest17<0>(a, b, md); pass = md <= bound; npd += 14; }
         d2 = md;
     }
-    if (pass) {
-        atomicMin(key + lo, pack_key(d2, s_sidx[j], o));
-        atomicMin(s_best + lo, __float_as_uint(d2));
+    float kf;
+    // a[63]: the fiber's length, b[0].w: the centroid's (the TN term)
+    if (pass && key_value(cls, d2, s_thr[j], a[NC], b[0].w, kf)) {
+        atomicMin(key + lo, pack_key(kf, s_sidx[j], o));
+        atomicMin(s_best + lo, __float_as_uint(kf));
     }
 }
 
@@ -1204,7 +1211,8 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 const float* a = s_fib + lo * FS_STRIDE;
                 const int j = INV ? bit : bit >> 1;
                 const float4* b = s_cen + j * CROW4;
-                const float bound = fminf(s_thr[j], __uint_as_float(s_best[lo]));
+                const float bound =
+                    fminf(s_thr[j], key_bound2(__uint_as_float(s_best[lo]), at.cls));
                 const float c = pd2v(a, CENTRE, b, CENTRE);
                 npd += 1;
                 if (c <= bound) {
@@ -1215,10 +1223,25 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                         mr = fmaxf(c, ends2<1>(a, b));
                         ad = md <= bound;
                         ar = mr <= bound;
+                        if (at.cls == CLS_PAPER) {  // direction inferred from the end points
+                            const bool direct = md <= mr;
+                            ad = ad && direct;
+                            ar = ar && !direct;
+                        }
                     } else {
                         md = fmaxf(c, (bit & 1) ? ends2<1>(a, b) : ends2<0>(a, b));
                         npd += 2;
                         ad = md <= bound;
+                        if (at.cls == CLS_PAPER) {  // this column's orientation must be the
+                            // one the end points infer (the other column, if it survived the
+                            // screen, carries the other)
+                            const float other = fmaxf(c, (bit & 1) ? ends2<0>(a, b)
+                                                                   : ends2<1>(a, b));
+                            npd += 2;
+                            const float dmax = (bit & 1) ? other : md;  // direct
+                            const float rmax = (bit & 1) ? md : other;  // reversed
+                            ad = ad && (((bit & 1) == 0) == (dmax <= rmax));
+                        }
                     }
                     push = ad || ar;
                     ent = (unsigned)lo | ((unsigned)bit << 5) | ((unsigned)ad << 10) |
@@ -1231,7 +1254,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             base = __shfl_sync(0xffffffffu, base, 0);
             if (push && base + __popc(bal & lt) >= EX_QLEN) {
                 exact_entry<INV>(ent, make_float2(md, mr), s_fib, s_cen, s_thr, s_sidx, s_best,
-                                 g.key + h.x, npd);
+                                 g.key + h.x, npd, at.cls);
                 push = false;
             }
             if (push) {
@@ -1250,7 +1273,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         if (tid < 32 && s_first[tid] != ~0u) {
             const unsigned q = s_first[tid] & 511u;
             exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_thr, s_sidx, s_best, g.key + h.x,
-                             npd);
+                             npd, at.cls);
             s_q[q] = DONE_ENTRY;
         }
         __syncthreads();
@@ -1259,7 +1282,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             const unsigned ent = s_q[q];
             if (ent != DONE_ENTRY)
                 exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_thr, s_sidx, s_best, g.key + h.x,
-                                 npd);
+                                 npd, at.cls);
         }
         __syncthreads();  // the buffers are refilled for the next record
     }
@@ -1276,12 +1299,16 @@ __device__ __noinline__ void rescan_fiber(long long f, const AtlasView& at, cons
     float a[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) a[k] = __ldg(src + k);
+    const float ls = __ldg(src + NC);  // the fiber's length (TN term)
     for (int s = 0; s < at.M; ++s) {
-        const float bound = fminf(__ldg(at.thr2 + s), __uint_as_float((unsigned)(g.key[f] >> 32)));
-        float d2;
+        const float t2 = __ldg(at.thr2 + s);
+        const float bound =
+            fminf(t2, key_bound2(__uint_as_float((unsigned)(g.key[f] >> 32)), at.cls));
+        float d2, kf;
         int o;
-        if (exact_pair(a, at.cen + (size_t)s * CROW, bound, d2, o))
-            atomicMin(g.key + f, pack_key(d2, s, o));
+        if (exact_pair(a, at.cen + (size_t)s * CROW, bound, d2, o, at.cls) &&
+            key_value(at.cls, d2, t2, ls, __ldg(at.cen + (size_t)s * CROW + NC), kf))
+            atomicMin(g.key + f, pack_key(kf, s, o));
     }
 }
 
@@ -1326,7 +1353,8 @@ __global__ void k_finalize(long long n, AtlasView at, GemmScratch g, FiberSrc sr
     }
     const int s = (int)((k & 0xffffffffull) >> 1);
     labels[o] = at.bundle[s];
-    if (dist) dist[o] = sqrtf(__uint_as_float((unsigned)(k >> 32)));
+    const float kf = __uint_as_float((unsigned)(k >> 32));
+    if (dist) dist[o] = at.cls != 0 ? kf : sqrtf(kf);  // D, or sqrt(d^2)
     if (cidx) cidx[o] = at.perm[s];
     if (orient) orient[o] = (unsigned char)(k & 1ull);
 }
@@ -1727,7 +1755,7 @@ seg_status gemm_batch_launch(const AtlasView& at, GemmAtlas* ga, ScratchArena* s
     if (s != SEG_OK) return s;
     cudaError_t e = cudaSuccess;
     if (!b->graph_exec || b->mode != mode || b->config != config || b->nsubj != nsubj ||
-        b->total != total || b->scratch_ptr != c.g.a) {
+        b->total != total || b->scratch_ptr != c.g.a || b->cls != at.cls) {
         if (b->graph_exec) {
             cudaGraphExecDestroy((cudaGraphExec_t)b->graph_exec);
             b->graph_exec = nullptr;
@@ -1755,6 +1783,7 @@ seg_status gemm_batch_launch(const AtlasView& at, GemmAtlas* ga, ScratchArena* s
         b->nsubj = nsubj;
         b->total = total;
         b->scratch_ptr = c.g.a;
+        b->cls = at.cls;
     }
     e = cudaMemcpyAsync(b->table, host_table, table_bytes, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaEventRecord((cudaEvent_t)copied_event, st);

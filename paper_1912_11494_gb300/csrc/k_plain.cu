@@ -39,7 +39,8 @@ struct WarpSmem {
     static constexpr size_t fc_off = 0;                        // [TW][63] floats
     static constexpr size_t fs_off = fc_off + TW * NC * 4;     // [TW][2] float4
     static constexpr size_t key_off = fs_off + TW * 32;        // [TW] u64
-    static constexpr size_t q_off = key_off + TW * 8;          // [QW] u32
+    static constexpr size_t ls_off = key_off + TW * 8;         // [TW] fiber lengths (TN)
+    static constexpr size_t q_off = ls_off + TW * 4;           // [QW] u32
     static constexpr size_t bar_off = (q_off + QW * 4 + 15) / 16 * 16;
     static constexpr size_t bytes = bar_off + 16;
 };
@@ -74,7 +75,8 @@ __device__ __forceinline__ float key_best2(unsigned long long k) {
 // fiber's key. The centroid row (256 B, aligned) is loaded in one batch of 16-byte loads so a
 // check costs one memory round trip; the fiber comes from shared memory.
 __device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float* fc,
-                                                unsigned long long* key, unsigned e) {
+                                                const float* ls, unsigned long long* key,
+                                                unsigned e) {
     const int c = (int)(e >> 8);
     const int f = (int)(e & 255u);
     float b[CROW];
@@ -87,11 +89,14 @@ __device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float
         b[4 * q + 2] = v.z;
         b[4 * q + 3] = v.w;
     }
-    const float bound = fminf(__ldg(at.thr2 + c), key_best2(key[f]));
-    float d2;
+    const float t2 = __ldg(at.thr2 + c);
+    const float bound = fminf(t2, key_bound2(key_best2(key[f]), at.cls));
+    float d2, kf;
     int o;
-    if (exact_pair(fc + f * NC, b, bound, d2, o)) {
-        const unsigned long long k = ((unsigned long long)__float_as_uint(d2) << 32) |
+    // b[63] is the centroid's length (the TN term of Eq. 3)
+    if (exact_pair(fc + f * NC, b, bound, d2, o, at.cls) &&
+        key_value(at.cls, d2, t2, ls[f], b[CROW - 1], kf)) {
+        const unsigned long long k = ((unsigned long long)__float_as_uint(kf) << 32) |
                                      ((unsigned long long)c << 1) | (unsigned)o;
         atomicMin(key + f, k);
     }
@@ -112,6 +117,7 @@ __device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long l
     float* fc = reinterpret_cast<float*>(ws + WS::fc_off);
     float4* fs = reinterpret_cast<float4*>(ws + WS::fs_off);
     unsigned long long* key = reinterpret_cast<unsigned long long*>(ws + WS::key_off);
+    float* ls = reinterpret_cast<float*>(ws + WS::ls_off);
     unsigned* q = reinterpret_cast<unsigned*>(ws + WS::q_off);
     uint64_t* bar = reinterpret_cast<uint64_t*>(ws + WS::bar_off);
     const int nf = (int)min((long long)TW, n - f0);
@@ -160,6 +166,7 @@ __device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long l
         }
         fs[2 * lane] = make_float4(x, x, y, y);
         fs[2 * lane + 1] = make_float4(z, z, h, h);
+        ls[lane] = at.cls != 0 && lane < nf ? poly_length(fc + lane * NC) : 0.0f;
     }
     __syncwarp();
 
@@ -260,7 +267,7 @@ __device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long l
             }
         }
         __syncwarp();
-        for (int i = lane; i < qn; i += 32) exact_and_merge(at, fc, key, q[i]);
+        for (int i = lane; i < qn; i += 32) exact_and_merge(at, fc, ls, key, q[i]);
         __syncwarp();
         if (!full) break;
     }
@@ -281,7 +288,8 @@ __device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long l
         } else {
             const int c = (int)((k & 0xffffffffull) >> 1);
             labels[gi] = at.bundle[c];
-            if (dist) dist[gi] = sqrtf(__uint_as_float((unsigned)(k >> 32)));
+            const float kf = __uint_as_float((unsigned)(k >> 32));
+            if (dist) dist[gi] = at.cls != 0 ? kf : sqrtf(kf);  // D, or sqrt(d^2)
             if (cidx) cidx[gi] = at.perm[c];
             if (orient) orient[gi] = (unsigned char)(k & 1ull);
         }

@@ -78,8 +78,15 @@ __global__ void k_prep_atlas(const float* __restrict__ cen, const int* __restric
     const int c = perm[s];
     const float* src = cen + (size_t)c * NC;
     float* dst = cs + (size_t)s * CROW;
-    for (int k = threadIdx.x; k < CROW; k += blockDim.x) dst[k] = k < NC ? src[k] : 0.0f;
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) dst[k] = src[k];
     if (threadIdx.x == 0) {
+        float len = 0.0f;  // the centroid's polyline length (Eq. 3's l_C) in the free slot
+        for (int i = 0; i + 1 < NPTS; ++i) {
+            const float dx = src[3 * i] - src[3 * i + 3], dy = src[3 * i + 1] - src[3 * i + 4],
+                        dz = src[3 * i + 2] - src[3 * i + 5];
+            len += sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+        dst[CROW - 1] = len;
         const int b = bundle_of[c];
         const float t = thr[b];
         const float t2 = t * t;
@@ -489,6 +496,24 @@ seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config) {
     if (config < 0 || config >= nc)
         return fail(SEG_ERR_INVALID_ARG, "seg_set_config: config %d outside [0,%d)", config, nc);
     atlas->config[(int)mode] = config;
+    return SEG_OK;
+}
+
+seg_status seg_set_classification(seg_atlas* atlas, seg_classification cls) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_classification: atlas is NULL");
+    if ((int)cls < SEG_CLASS_EQ2 || (int)cls > SEG_CLASS_PAPER)
+        return fail(SEG_ERR_INVALID_ARG, "seg_set_classification: unknown classification %d",
+                    (int)cls);
+    std::lock_guard<std::mutex> lock(atlas->mu);
+    atlas->view.cls = (int)cls;
+    return SEG_OK;
+}
+
+seg_status seg_get_classification(const seg_atlas* atlas, seg_classification* cls) {
+    g_last_error.clear();
+    if (!atlas || !cls) return fail(SEG_ERR_INVALID_ARG, "seg_get_classification: NULL argument");
+    *cls = (seg_classification)atlas->view.cls;
     return SEG_OK;
 }
 

@@ -72,6 +72,9 @@ struct AtlasView {
     const int* bundle;          // [M]: bundle index (caller numbering)
     const int* perm;            // [M]: caller's centroid index of sorted position
     unsigned* status;           // device status word
+    int cls;                    // classification: 0 Eq. 2, 1 Eq. 2 + TN, 2 the paper's
+                                // direction inference + TN (seg_classification); cen[63] of
+                                // each row holds the centroid's length for the TN term
 };
 
 // One subject of a batched call (device table; entry nsubj holds only tile0 = total tiles).

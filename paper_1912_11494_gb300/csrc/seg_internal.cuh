@@ -93,7 +93,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, 
 // back-to-back calls do not wait for each other on the host.
 struct BatchState {
     void* graph_exec = nullptr;   // cudaGraphExec_t
-    int mode = -1, nsubj = -1, config = -1;
+    int mode = -1, nsubj = -1, config = -1, cls = -1;
     long long total = -1;         // fibers of all subjects (GEMM modes: sizes the graph)
     void* scratch_ptr = nullptr;  // the scratch the GEMM graph was captured on
     void* table = nullptr;        // device BatchEntry[table_cap]
