@@ -57,11 +57,13 @@ def _bind(lib):
     lib.oracle_near_tie_cls.argtypes = [P, I64, P, P, I64, P, I32, ctypes.c_int, P, P,
                                         ctypes.c_double, P, ctypes.c_int]
     lib.oracle_lengths.argtypes = [P, I64, P]
+    lib.oracle_resample.argtypes = [P, P, I64, P, ctypes.c_int]
     lib.oracle_grad.argtypes = [P, I64, P, P, P, I64, P, I32, P, P, P, P, P, P, P, P, P, P, P,
                                 ctypes.c_int]
     for f in (lib.oracle_dme_matrix, lib.oracle_label_brute, lib.oracle_label_cascade,
               lib.oracle_near_tie, lib.oracle_near_tie_pruned, lib.oracle_dme_pairs,
               lib.oracle_label_cls, lib.oracle_near_tie_cls, lib.oracle_lengths,
+              lib.oracle_resample,
               lib.oracle_grad):
         f.restype = ctypes.c_int
     return lib
@@ -208,6 +210,17 @@ def near_tie_cls(fibers, centroids, bundle_of, thresholds, cls: str, labels, dis
                                        _ptr(thr), thr.shape[0], CLASSIFICATIONS[cls], _ptr(lab),
                                        _ptr(dist), tol, _ptr(flag), nthreads))
     return flag
+
+
+def resample(points, offsets, nthreads: int = 0):
+    """21 arc-length-equidistant points of each raw streamline (CSR: points float32 [P, 3],
+    offsets int64 [n+1]), float64 [n, 21, 3] (Section 2.3)."""
+    pts = _f32(points).reshape(-1, 3)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = off.shape[0] - 1
+    out = np.empty((n, 21, 3))
+    _check(_load().oracle_resample(_ptr(pts), _ptr(off), n, _ptr(out), nthreads))
+    return out
 
 
 def lengths(fibers):

@@ -658,6 +658,55 @@ int oracle_lengths(const float *fib, int64_t n, double *len) {
     return 0;
 }
 
+/* ---- resampling of raw streamlines (Section 2.3) ----------------------------------------- */
+
+/* "Subject fibers are resampled using 21 equidistant points" (Section 2.3), read as equidistant
+ * in arc length along the streamline's polyline: with cumulative lengths c_0 = 0 <= c_1 <= ...
+ * <= c_(m-1) = L over its m points, output point k (0 <= k <= 20) is the point at arc length
+ * s_k = k L / 20, linearly interpolated inside the first segment (j, j+1) with c_j < s_k <=
+ * c_(j+1) (zero-length segments never hold one); point 0 is the first point and point 20 the
+ * last. A streamline with a single point, or of zero length, gives 21 copies of its first
+ * point; one with no points gives NaN. points [P][3], offsets [n+1] (fiber f has points
+ * offsets[f] .. offsets[f+1]-1), out [n][21][3] in double. */
+int oracle_resample(const float *points, const int64_t *offsets, int64_t n, double *out,
+                    int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t f = 0; f < n; ++f) {
+        const int64_t p0 = offsets[f], m = offsets[f + 1] - offsets[f];
+        double *o = out + f * NC;
+        if (m <= 0) {
+            for (int k = 0; k < NC; ++k) o[k] = NAN;
+            continue;
+        }
+        double *q = malloc((size_t)m * 3 * sizeof(double));
+        double *c = malloc((size_t)m * sizeof(double));
+        promote(points + 3 * p0, q, 3 * m);
+        c[0] = 0.0;
+        for (int64_t j = 0; j + 1 < m; ++j) c[j + 1] = c[j] + d_E(q + 3 * j, q + 3 * (j + 1));
+        const double L = c[m - 1];
+        for (int r = 0; r < 3; ++r) {
+            o[r] = q[r];
+            o[3 * (NPTS - 1) + r] = q[3 * (m - 1) + r];
+        }
+        int64_t j = 0;
+        for (int k = 1; k < NPTS - 1; ++k) {
+            if (!(L > 0.0)) {
+                for (int r = 0; r < 3; ++r) o[3 * k + r] = q[r];
+                continue;
+            }
+            const double sk = k * L / (NPTS - 1);
+            while (j + 1 < m - 1 && !(c[j] < sk && sk <= c[j + 1])) ++j;
+            const double w = (sk - c[j]) / (c[j + 1] - c[j]);
+            for (int r = 0; r < 3; ++r)
+                o[3 * k + r] = q[3 * j + r] + w * (q[3 * (j + 1) + r] - q[3 * j + r]);
+        }
+        free(q);
+        free(c);
+    }
+    return 0;
+}
+
 /* y = M x + t for every point, in double. aff = M row-major (9) then t (3). */
 static void apply_affine(const double *aff, const double *x, double *y) {
     for (int p = 0; p < NPTS; ++p) {

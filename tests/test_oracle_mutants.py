@@ -37,6 +37,10 @@ MUTANTS = {
     "tn_squared_ratio": ("return (r + 1.0) * (r + 1.0) - 1.0;", "return r * r;"),
     "length_drops_a_segment": ("for (int i = 0; i + 1 < NPTS; ++i) l += d_E",
                                "for (int i = 1; i + 1 < NPTS; ++i) l += d_E"),
+    "resample_by_index": ("const double sk = k * L / (NPTS - 1);",
+                          "const double sk = c[(m - 1) * k / (NPTS - 1)];"),
+    "resample_no_interpolation": ("o[3 * k + r] = q[3 * j + r] + w * (q[3 * (j + 1) + r] - q[3 * j + r]);",
+                                  "o[3 * k + r] = q[3 * j + r];"),
     "inference_takes_larger": ("int o = ed <= er ? 0 : 1; /* direction inference */",
                                "int o = ed <= er ? 1 : 0; /* direction inference */"),
     "inference_skipped": ("    m = o ? er : ed;\n    for (int q = 0; q < 4; ++q) { /* test3 */",
@@ -55,7 +59,8 @@ PINS = [pins.test_worked_examples_dme, pins.test_worked_examples_labels,
         pins.test_grad_reversed_orientation_closed_form,
         pins.test_grad_frozen_structure_fd, pins.test_lengths_closed_forms,
         pins.test_tn_worked_example,
-        pins.test_direction_inference_can_miss_the_closer_orientation]
+        pins.test_direction_inference_can_miss_the_closer_orientation,
+        pins.test_resample_closed_forms]
 
 
 def _gold():

@@ -400,6 +400,30 @@ def test_near_tie_cls_flags_ambiguous_direction():
     assert flag[1] == 0
 
 
+def test_resample_closed_forms():
+    """Arc-length resampling to 21 points (Section 2.3): a straight streamline with uneven
+    vertex spacing resamples to x = k L / 20 exactly; 201 vertices at equal angle steps on a
+    circle (200 equal chords) resample onto vertices 0, 10, ..., 200; a zero-length segment
+    (a repeated vertex) changes nothing; a single point gives 21 copies; no point gives NaN."""
+    line = np.array([[0, 0, 0], [1, 0, 0], [5, 0, 0], [5, 0, 0], [20, 0, 0]], np.float32)
+    R = 9.0
+    ang = np.linspace(0.0, 1.5 * np.pi, 201)
+    circ = np.stack([R * np.cos(ang), R * np.sin(ang), 0 * ang], axis=1).astype(np.float32)
+    single = np.array([[3, -2, 7]], np.float32)
+    pts = np.concatenate([line, circ, single])
+    off = np.array([0, 5, 206, 207, 207], np.int64)  # the last streamline has no point
+    r = oracle.resample(pts, off)
+    np.testing.assert_allclose(r[0, :, 0], np.arange(21.0), atol=1e-12)
+    assert not r[0, :, 1:].any()
+    np.testing.assert_allclose(r[1], circ[::10].astype(np.float64), atol=1e-5)
+    np.testing.assert_array_equal(r[2], np.repeat(single.astype(np.float64), 21, axis=0))
+    assert np.isnan(r[3]).all()
+    # resampling an already equidistant 21-point fiber returns it
+    t = np.arange(21, dtype=np.float32)
+    fib = np.stack([2 * t, 0 * t, 0 * t], axis=1)
+    np.testing.assert_allclose(oracle.resample(fib, [0, 21])[0], fib, atol=1e-12)
+
+
 def test_grad_translation_closed_form():
     """One fiber, one centroid, translation only: dC/dt = u = r/|r| at the argmax point."""
     t = np.arange(21, dtype=np.float32)
