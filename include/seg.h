@@ -163,6 +163,34 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
                           seg_mode mode, int32_t* h_labels, float* h_dist, void* stream);
 
 /*
+ * Resample raw streamlines to the 21 arc-length-equidistant points the labelling takes
+ * (Section 2.3: subject fibers are resampled using 21 equidistant points; the paper's
+ * tractography steps 0.2 mm, Section 2.1). Not tied to an atlas.
+ *   d_points  device float32 [P][3]: the points of every streamline, one streamline after
+ *             another (4-byte aligned).
+ *   d_offsets device int64 [n + 1] (8-byte aligned): streamline f has the points
+ *             d_offsets[f] .. d_offsets[f+1] - 1; non-decreasing from d_offsets[0] = 0 (read on
+ *             the device and not validated: a decreasing entry gives an empty streamline).
+ *   d_out     device float32 [n][21][3].
+ * Output point k is the point at arc length k L / 20 along the polyline (L its length; linear
+ * interpolation inside the segment that reaches it); points 0 and 20 are the end points. A
+ * streamline with one point, or of zero length, gives 21 copies of its first point; one with
+ * no point gives NaN coordinates (such a fiber is labelled -1 with distance NaN).
+ */
+seg_status seg_resample(const float* d_points, const int64_t* d_offsets, int64_t n, float* d_out,
+                        void* stream);
+
+/*
+ * seg_resample, then seg_label on the 21-point fibers it produced (held in atlas-owned scratch,
+ * grown on demand and released stream-ordered): raw tractography in, labels out. Outputs and
+ * modes as seg_label.
+ */
+seg_status seg_label_streamlines(const seg_atlas* atlas, const float* d_points,
+                                 const int64_t* d_offsets, int64_t n, seg_mode mode,
+                                 int32_t* d_labels, float* d_dist, int32_t* d_cidx,
+                                 uint8_t* d_orient, void* stream);
+
+/*
  * Label nsubj subjects of uneven size together (not in the paper; the paper labels one subject
  * at a time, Section 3). Subject s has h_counts[s] >= 0 fibers at device pointer h_fibers[s]
  * and writes h_labels[s] (required) and h_dist[s] (array or entries may be NULL). The pointer

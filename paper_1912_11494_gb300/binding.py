@@ -45,6 +45,9 @@ SIGNATURES = [
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    ("seg_resample", ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    ("seg_label_streamlines", ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P, _P, _P, _P,
+                                             _P]),
     ("seg_set_classification", ctypes.c_int, [_P, ctypes.c_int]),
     ("seg_get_classification", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("seg_gemm_screen_bits", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P]),
@@ -256,6 +259,34 @@ def seg_gemm_screen_bits(atlas: Atlas, fibers, mode, stream=None):
     _check(lib().seg_gemm_screen_bits(atlas.handle, _ptr(fib), int(fib.shape[0]), m,
                                       _ptr(bits), words, _stream(stream)))
     return bits
+
+
+def seg_resample(points, offsets, out=None, stream=None):
+    """21 arc-length-equidistant points per raw streamline: points CUDA float32 [P, 3], offsets
+    CUDA int64 [n + 1]; returns (or fills) float32 [n, 21, 3]."""
+    pts = _dev(points, torch.float32, "points").contiguous()
+    off = _dev(offsets, torch.int64, "offsets").contiguous()
+    n = int(off.shape[0]) - 1
+    if out is None:
+        out = torch.empty((n, NPTS, 3), dtype=torch.float32, device=pts.device)
+    _check(lib().seg_resample(_ptr(pts), _ptr(off), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def label_streamlines(atlas: Atlas, points, offsets, mode="plain", stream=None):
+    """Resample raw streamlines and label them: returns (labels, dist, cidx, orient)."""
+    pts = _dev(points, torch.float32, "points").contiguous()
+    off = _dev(offsets, torch.int64, "offsets").contiguous()
+    n = int(off.shape[0]) - 1
+    dev = pts.device
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    dist = torch.empty(n, dtype=torch.float32, device=dev)
+    cidx = torch.empty(n, dtype=torch.int32, device=dev)
+    orient = torch.empty(n, dtype=torch.uint8, device=dev)
+    _check(lib().seg_label_streamlines(atlas.handle, _ptr(pts), _ptr(off), n, _mode(mode),
+                                       _ptr(labels), _ptr(dist), _ptr(cidx), _ptr(orient),
+                                       _stream(stream)))
+    return labels, dist, cidx, orient
 
 
 CLASSIFICATIONS = {"eq2": 0, "eq2_tn": 1, "paper": 2}

@@ -134,6 +134,8 @@ struct seg_atlas {
     unsigned* status = nullptr;
     GemmAtlas gemm{};
     ScratchArena scratch{};
+    ScratchArena rs_scratch{};  // seg_label_streamlines: the resampled fibers (guarded by rs_mu)
+    std::mutex rs_mu;
     // seg_label_host: two device copies of the caller's host buffers, used by alternate calls
     // (so that a call's upload overlaps the previous call's labelling), an internal copy
     // stream, one event per chunk and one per buffer marking its last use (guarded by
@@ -179,6 +181,7 @@ static void free_atlas(seg_atlas* a) {
     cudaFree(a->status);
     free_gemm_atlas(&a->gemm);
     free_scratch(&a->scratch);
+    free_scratch(&a->rs_scratch);
     if (a->hcopy) cudaStreamSynchronize(a->hcopy);
     for (cudaEvent_t ev : a->hev)
         if (ev) cudaEventDestroy(ev);
@@ -414,6 +417,49 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
     }
     if ((e = cudaEventRecord(ev_done, st))) return cuda_fail(e, "seg_label_host: event");
     return SEG_OK;
+}
+
+seg_status seg_resample(const float* d_points, const int64_t* d_offsets, int64_t n, float* d_out,
+                        void* stream) {
+    g_last_error.clear();
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_resample: n=%lld < 0", (long long)n);
+    if (n == 0) return SEG_OK;
+    if (!d_offsets || !d_out)
+        return fail(SEG_ERR_INVALID_ARG, "seg_resample: NULL offsets or output");
+    if (unaligned4(d_points) || unaligned4(d_out) ||
+        (reinterpret_cast<uintptr_t>(d_offsets) & 7u))
+        return fail(SEG_ERR_INVALID_ARG, "seg_resample: a buffer is not aligned");
+    return resample_launch(d_points, reinterpret_cast<const long long*>(d_offsets), n, d_out,
+                           (cudaStream_t)stream);
+}
+
+seg_status seg_label_streamlines(const seg_atlas* atlas, const float* d_points,
+                                 const int64_t* d_offsets, int64_t n, seg_mode mode,
+                                 int32_t* d_labels, float* d_dist, int32_t* d_cidx,
+                                 uint8_t* d_orient, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: n < 0");
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: unknown mode %d", (int)mode);
+    if (n == 0) return SEG_OK;
+    if (!d_offsets || !d_labels)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: NULL offsets or labels");
+    if (unaligned4(d_points) || unaligned4(d_labels) || unaligned4(d_dist) ||
+        unaligned4(d_cidx) || (reinterpret_cast<uintptr_t>(d_offsets) & 7u))
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: a buffer is not aligned");
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(a->rs_mu);  // one user of rs_scratch at a time
+    void* buf = nullptr;
+    seg_status s = scratch_acquire(&a->rs_scratch, (size_t)n * NC * sizeof(float), st, &buf);
+    if (s != SEG_OK) return s;
+    float* fib = static_cast<float*>(buf);
+    s = resample_launch(d_points, reinterpret_cast<const long long*>(d_offsets), n, fib, st);
+    if (s == SEG_OK)
+        s = seg_label(atlas, fib, n, mode, d_labels, d_dist, d_cidx, d_orient, stream);
+    const seg_status r = scratch_release(&a->rs_scratch, st);
+    return s != SEG_OK ? s : r;
 }
 
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,

@@ -161,7 +161,8 @@ def make_subject(atlas: Atlas, n: int, bundle_frac: float, seed: int, sigma: flo
     return _subject_from_rng(rng, atlas, n, bundle_frac, sigma, device)
 
 
-def _subject_from_rng(rng, atlas: Atlas, n: int, bundle_frac: float, sigma: float, device):
+def _subject_ctrl(rng, atlas: Atlas, n: int, bundle_frac: float, sigma: float, device):
+    """Control points of a subject's curves, which are reversed, and the shuffle."""
     nb = int(round(bundle_frac * n))
     nn = n - nb
     bid = rng.integers(0, atlas.B, size=nb)
@@ -170,9 +171,48 @@ def _subject_from_rng(rng, atlas: Atlas, n: int, bundle_frac: float, sigma: floa
     ctrl = np.concatenate([ctrl_b, ctrl_n], axis=0)
     rev = rng.random(n) < 0.5
     perm = rng.permutation(n)
+    return ctrl, rev, perm
+
+
+def _subject_from_rng(rng, atlas: Atlas, n: int, bundle_frac: float, sigma: float, device):
+    ctrl, rev, perm = _subject_ctrl(rng, atlas, n, bundle_frac, sigma, device)
     fib = _resample_ctrl(ctrl, device)
     fib[rev] = fib[rev, ::-1]
     return np.ascontiguousarray(fib[perm])
+
+
+STEP_MM = 0.2  # tractography step of the paper's data (Section 2.1)
+
+
+def make_streamlines(atlas: Atlas, n: int, bundle_frac: float, seed: int, sigma: float = 2.0,
+                     step: float = STEP_MM, device="cpu", chunk: int = 1 << 17):
+    """Raw (not resampled) streamlines of the subject recipe, as CSR arrays on `device`:
+    points float32 [P, 3] and offsets int64 [n + 1]. Each curve (the same control points,
+    reversals and shuffle as make_subject with this seed) is evaluated at K = round(L / step) + 1
+    Bezier parameters spaced uniformly in [0, 1], so consecutive points are about `step` mm apart
+    on average but unevenly spaced in arc length."""
+    ctrl, rev, perm = _subject_ctrl(_rng(seed), atlas, n, bundle_frac, sigma, device)
+    ctrl = ctrl[perm]
+    rev = rev[perm]
+    pts_out, counts = [], []
+    for s0 in range(0, n, chunk):
+        c = torch.from_numpy(np.ascontiguousarray(ctrl[s0:s0 + chunk])).to(device)
+        L = _arc_length(_dense(c))
+        k = torch.clamp(torch.round(L / step).to(torch.int64) + 1, min=2)
+        fid = torch.repeat_interleave(torch.arange(c.shape[0], device=device), k)
+        start = torch.cumsum(k, 0) - k
+        idx = torch.arange(fid.shape[0], device=device) - start[fid]
+        t = idx.to(torch.float64) / (k[fid] - 1).to(torch.float64)
+        r = torch.from_numpy(rev[s0:s0 + chunk]).to(device)[fid]
+        t = torch.where(r, 1.0 - t, t)
+        u = 1.0 - t
+        bern = torch.stack([u * u * u, 3 * u * u * t, 3 * u * t * t, t * t * t], dim=1)
+        pts_out.append(torch.einsum("pk,pkc->pc", bern, c[fid]).to(torch.float32))
+        counts.append(k)
+    counts = torch.cat(counts)
+    offsets = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    offsets[1:] = torch.cumsum(counts, 0)
+    return torch.cat(pts_out).contiguous(), offsets
 
 
 def batch_counts(nsubj: int = 16, lo: float = 3e5, hi: float = 4.2e6) -> list[int]:

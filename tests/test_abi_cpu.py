@@ -68,6 +68,11 @@ def test_argument_errors_before_device_work(lib):
     assert lib.seg_apply_affine(None, -1, None, None, None) == 1
     assert lib.seg_apply_affine(None, 0, None, None, None) == 1
     assert lib.seg_gemm_stats(None, None, None, None, None, None) == 1
+    assert lib.seg_resample(None, None, -1, None, None) == 1
+    assert lib.seg_resample(None, None, 0, None, None) == 0
+    assert lib.seg_resample(None, None, 5, None, None) == 1
+    assert lib.seg_label_streamlines(None, None, None, 0, 0, None, None, None, None, None) == 1
+    assert lib.seg_set_classification(None, 0) == 1
     # a float buffer that is not 4-byte aligned is refused before it is touched
     aff = (ctypes.c_double * 12)()
     assert lib.seg_apply_affine(ctypes.c_void_p(0x1002), 1, aff, ctypes.c_void_p(0x2000),
