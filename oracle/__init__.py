@@ -58,12 +58,14 @@ def _bind(lib):
                                         ctypes.c_double, P, ctypes.c_int]
     lib.oracle_lengths.argtypes = [P, I64, P]
     lib.oracle_resample.argtypes = [P, P, I64, P, ctypes.c_int]
+    lib.oracle_label_multi.argtypes = [P, I64, P, P, I64, P, I32, ctypes.c_int, I64, P, P,
+                                       ctypes.c_double, ctypes.c_int]
     lib.oracle_grad.argtypes = [P, I64, P, P, P, I64, P, I32, P, P, P, P, P, P, P, P, P, P, P,
                                 ctypes.c_int]
     for f in (lib.oracle_dme_matrix, lib.oracle_label_brute, lib.oracle_label_cascade,
               lib.oracle_near_tie, lib.oracle_near_tie_pruned, lib.oracle_dme_pairs,
               lib.oracle_label_cls, lib.oracle_near_tie_cls, lib.oracle_lengths,
-              lib.oracle_resample,
+              lib.oracle_resample, lib.oracle_label_multi,
               lib.oracle_grad):
         f.restype = ctypes.c_int
     return lib
@@ -221,6 +223,24 @@ def resample(points, offsets, nthreads: int = 0):
     out = np.empty((n, 21, 3))
     _check(_load().oracle_resample(_ptr(pts), _ptr(off), n, _ptr(out), nthreads))
     return out
+
+
+def label_multi(fibers, centroids, bundle_of, thresholds, cls: str = "eq2",
+                tol: float = 2e-3, nthreads: int = 0):
+    """Every bundle each fiber passes (Section 2.4): (bits, ambiguous), uint32 [n, ceil(B/32)]
+    bit rows; ambiguous marks bundles whose best centroid lies within tol of its threshold."""
+    fib = _f32(fibers).reshape(-1, 63)
+    cen = _f32(centroids).reshape(-1, 63)
+    bo = np.ascontiguousarray(bundle_of, dtype=np.int32)
+    thr = _f32(thresholds)
+    n, B = fib.shape[0], thr.shape[0]
+    words = (B + 31) // 32
+    bits = np.empty((n, words), np.uint32)
+    amb = np.empty((n, words), np.uint32)
+    _check(_load().oracle_label_multi(_ptr(fib), n, _ptr(cen), _ptr(bo), cen.shape[0], _ptr(thr),
+                                      B, CLASSIFICATIONS[cls], words, _ptr(bits), _ptr(amb), tol,
+                                      nthreads))
+    return bits, amb
 
 
 def lengths(fibers):

@@ -707,6 +707,68 @@ int oracle_resample(const float *points, const int64_t *offsets, int64_t n, doub
     return 0;
 }
 
+/* ---- multi-label output (Section 2.4, "Classification of fibers") ------------------------ */
+
+/* Every bundle a fiber passes: bit b of fiber f's row (words uint32 words) is set when some
+ * centroid of bundle b passes its threshold under classification cls (0 Eq. 2: d_ME <= theta;
+ * 1 and 2: D <= theta as in oracle_label_cls), which is how the paper's original algorithm could
+ * assign a fiber to several bundles. amb (optional, same shape) marks the bundles whose bit is
+ * not decidable at tolerance tol: no centroid of the bundle is below theta - tol but one is
+ * within tol of theta. Non-finite fibers get no bit. */
+int oracle_label_multi(const float *fib, int64_t n, const float *cen, const int32_t *bundle_of,
+                       int64_t M, const float *thr, int32_t B, int cls, int64_t words,
+                       uint32_t *bits, uint32_t *amb, double tol, int nthreads) {
+    if (cls < 0 || cls > 2 || words * 32 < B) return 2;
+    double *C = malloc((size_t)(M > 0 ? M : 1) * NC * sizeof(double));
+    double *L = malloc((size_t)(M > 0 ? M : 1) * sizeof(double));
+    if (!C || !L) {
+        free(C);
+        free(L);
+        return 1;
+    }
+    promote(cen, C, M * NC);
+    for (int64_t c = 0; c < M; ++c) L[c] = poly_length(C + c * NC);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t f = 0; f < n; ++f) {
+        uint32_t *row = bits + f * words, *arow = amb ? amb + f * words : NULL;
+        for (int64_t w = 0; w < words; ++w) {
+            row[w] = 0;
+            if (arow) arow[w] = 0;
+        }
+        double a[NC];
+        promote(fib + f * NC, a, NC);
+        if (!all_finite(a)) continue;
+        const double ls = poly_length(a);
+        /* per bundle: the smallest classification distance minus theta */
+        double *best = malloc((size_t)B * sizeof(double));
+        for (int32_t b = 0; b < B; ++b) best[b] = INFINITY;
+        for (int64_t c = 0; c < M; ++c) {
+            const double th = (double)thr[bundle_of[c]];
+            double D;
+            if (cls == 0) {
+                double dd, dr;
+                dme_both(a, C + c * NC, &dd, &dr);
+                D = dd <= dr ? dd : dr;
+            } else {
+                int o = 0;
+                /* with TN the gate is D itself; a large threshold keeps cls_distance from
+                 * discarding pairs just above theta, which the ambiguity test needs */
+                D = cls_distance(cls, a, C + c * NC, th + tol, ls, L[c], &o);
+            }
+            if (D - th < best[bundle_of[c]]) best[bundle_of[c]] = D - th;
+        }
+        for (int32_t b = 0; b < B; ++b) {
+            if (best[b] <= 0.0) row[b >> 5] |= 1u << (b & 31);
+            if (arow && fabs(best[b]) <= tol) arow[b >> 5] |= 1u << (b & 31);
+        }
+        free(best);
+    }
+    free(C);
+    free(L);
+    return 0;
+}
+
 /* y = M x + t for every point, in double. aff = M row-major (9) then t (3). */
 static void apply_affine(const double *aff, const double *x, double *y) {
     for (int p = 0; p < NPTS; ++p) {

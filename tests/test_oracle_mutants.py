@@ -41,6 +41,8 @@ MUTANTS = {
                           "const double sk = c[(m - 1) * k / (NPTS - 1)];"),
     "resample_no_interpolation": ("o[3 * k + r] = q[3 * j + r] + w * (q[3 * (j + 1) + r] - q[3 * j + r]);",
                                   "o[3 * k + r] = q[3 * j + r];"),
+    "multi_strict_threshold": ("if (best[b] <= 0.0) row[b >> 5] |= 1u << (b & 31);",
+                               "if (best[b] < 0.0) row[b >> 5] |= 1u << (b & 31);"),
     "inference_takes_larger": ("int o = ed <= er ? 0 : 1; /* direction inference */",
                                "int o = ed <= er ? 1 : 0; /* direction inference */"),
     "inference_skipped": ("    m = o ? er : ed;\n    for (int q = 0; q < 4; ++q) { /* test3 */",
@@ -60,7 +62,7 @@ PINS = [pins.test_worked_examples_dme, pins.test_worked_examples_labels,
         pins.test_grad_frozen_structure_fd, pins.test_lengths_closed_forms,
         pins.test_tn_worked_example,
         pins.test_direction_inference_can_miss_the_closer_orientation,
-        pins.test_resample_closed_forms]
+        pins.test_resample_closed_forms, pins.test_multi_label_hand_cases]
 
 
 def _gold():

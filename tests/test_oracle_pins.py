@@ -424,6 +424,31 @@ def test_resample_closed_forms():
     np.testing.assert_allclose(oracle.resample(fib, [0, 21])[0], fib, atol=1e-12)
 
 
+def test_multi_label_hand_cases():
+    """Every bundle a fiber passes (Section 2.4): a straight fiber against parallel copies at
+    distances 1 (bundle 2), 3 (bundle 0), 4.5 (bundle 1, threshold 4) and 6 (bundle 3,
+    threshold 7): d_ME of a parallel offset is the offset, so the fiber passes bundles 0, 2 and
+    3 (3 via a centroid farther than bundle 1's, which fails); the closest-bundle label is 2.
+    A second fiber far from everything passes none; a bundle at exactly its threshold passes
+    (d <= theta) and is flagged ambiguous."""
+    line = _line(1.0)
+    offs = [(0, 0, 3.0), (0, 4.5, 0), (0, 0, -1.0), (0, -6.0, 0), (5.0, 0, 0)]
+    cen = np.stack([line + np.array(o) for o in offs]).astype(np.float32)
+    bo = np.array([0, 1, 2, 3, 4], np.int32)
+    thr = np.array([5.0, 4.0, 5.0, 7.0, 5.0], np.float32)  # bundle 4: exactly at theta
+    fib = np.stack([line, line + [0, 0, 100.0]]).astype(np.float32)
+    bits, amb = oracle.label_multi(fib, cen, bo, thr)
+    assert bits.shape == (2, 1)
+    assert bits[0, 0] == (1 << 0) | (1 << 2) | (1 << 3) | (1 << 4)
+    assert bits[1, 0] == 0 and amb[1, 0] == 0
+    assert amb[0, 0] == 1 << 4
+    r = oracle.label(fib, cen, bo, thr)
+    assert r["labels"][0] == 2
+    # with TN (equal lengths: TN = 0) the same bundles
+    bits_tn, _ = oracle.label_multi(fib, cen, bo, thr, "eq2_tn")
+    np.testing.assert_array_equal(bits_tn, bits)
+
+
 def test_grad_translation_closed_form():
     """One fiber, one centroid, translation only: dC/dt = u = r/|r| at the argmax point."""
     t = np.arange(21, dtype=np.float32)
