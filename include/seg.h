@@ -147,6 +147,20 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
                      void* stream);
 
 /*
+ * Every bundle each fiber passes, besides the closest one (Section 2.4, "Classification of
+ * fibers": the paper's original algorithm could assign a fiber to several bundles; the new one
+ * keeps the closest). d_bundle_bits is device uint32 [n][words_per_fiber], overwritten: bit b
+ * of fiber f's row (word b / 32, bit b % 32) is set when some centroid of bundle b passes its
+ * threshold for f under the atlas's classification (d_ME <= theta, or D <= theta with TN).
+ * words_per_fiber >= ceil(B / 32). d_labels (required) and d_dist (or NULL) receive seg_label's
+ * closest-bundle result. Every passing pair is evaluated in full (no pruning by the best so far),
+ * so this costs more than seg_label on atlases whose bundles overlap.
+ */
+seg_status seg_label_multi(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                           seg_mode mode, uint32_t* d_bundle_bits, int64_t words_per_fiber,
+                           int32_t* d_labels, float* d_dist, void* stream);
+
+/*
  * seg_label on host buffers (not in the paper): h_fibers host float32 [n][21][3], h_labels host
  * int32 [n] (required), h_dist host float32 [n] or NULL. The subject is split into up to
  * SEG_HOST_CHUNKS chunks; chunk c+1 is uploaded on an internal stream while chunk c is labelled

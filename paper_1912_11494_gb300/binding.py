@@ -45,6 +45,7 @@ SIGNATURES = [
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    ("seg_label_multi", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P, _P, _P]),
     ("seg_resample", ctypes.c_int, [_P, _P, _I64, _P, _P]),
     ("seg_label_streamlines", ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P, _P, _P, _P,
                                              _P]),
@@ -259,6 +260,19 @@ def seg_gemm_screen_bits(atlas: Atlas, fibers, mode, stream=None):
     _check(lib().seg_gemm_screen_bits(atlas.handle, _ptr(fib), int(fib.shape[0]), m,
                                       _ptr(bits), words, _stream(stream)))
     return bits
+
+
+def label_multi(atlas: Atlas, fibers, mode="plain", stream=None):
+    """Every bundle each fiber passes: (bits int32 [n, ceil(B/32)] bit rows, labels, dist)."""
+    fib = _dev(fibers, torch.float32, "fibers").contiguous()
+    n = int(fib.shape[0])
+    words = (atlas.B + 31) // 32
+    bits = torch.empty((n, words), dtype=torch.int32, device=fib.device)
+    labels = torch.empty(n, dtype=torch.int32, device=fib.device)
+    dist = torch.empty(n, dtype=torch.float32, device=fib.device)
+    _check(lib().seg_label_multi(atlas.handle, _ptr(fib), n, _mode(mode), _ptr(bits), words,
+                                 _ptr(labels), _ptr(dist), _stream(stream)))
+    return bits, labels, dist
 
 
 def seg_resample(points, offsets, out=None, stream=None):

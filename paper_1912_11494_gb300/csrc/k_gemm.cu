@@ -1080,12 +1080,15 @@ template <bool INV>
 __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float* s_fib,
                                             const float4* s_cen, const float* s_thr,
                                             const int* s_sidx, unsigned* s_best,
-                                            unsigned long long* key, unsigned& npd, int cls) {
+                                            unsigned long long* key, unsigned& npd,
+                                            const AtlasView& at, const unsigned* perm) {
+    const int cls = at.cls;
     const int lo = (int)(ent & 31u), bit = (int)((ent >> 5) & 31u);
     const int j = INV ? bit : bit >> 1;
     const float* a = s_fib + lo * FS_STRIDE;
     const float4* b = s_cen + j * CROW4;
-    const float bound = fminf(s_thr[j], key_bound2(__uint_as_float(s_best[lo]), cls));
+    const float bound =
+        pair_bound2(at, s_thr[j], key_bound2(__uint_as_float(s_best[lo]), cls));
     float md = mm.x, mr = mm.y, d2;
     int o;
     bool pass;
@@ -1109,6 +1112,7 @@ __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float
     // a[63]: the fiber's length, b[0].w: the centroid's (the TN term)
     if (pass && key_value(cls, d2, s_thr[j], a[NC], b[0].w, kf)) {
         atomicMin(key + lo, pack_key(kf, s_sidx[j], o));
+        if (at.multi) multi_mark(at, perm[lo], at.bundle[s_sidx[j]]);
         atomicMin(s_best + lo, __float_as_uint(kf));
     }
 }
@@ -1212,7 +1216,8 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
                 const int j = INV ? bit : bit >> 1;
                 const float4* b = s_cen + j * CROW4;
                 const float bound =
-                    fminf(s_thr[j], key_bound2(__uint_as_float(s_best[lo]), at.cls));
+                    pair_bound2(at, s_thr[j],
+                                key_bound2(__uint_as_float(s_best[lo]), at.cls));
                 const float c = pd2v(a, CENTRE, b, CENTRE);
                 npd += 1;
                 if (c <= bound) {
@@ -1254,7 +1259,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             base = __shfl_sync(0xffffffffu, base, 0);
             if (push && base + __popc(bal & lt) >= EX_QLEN) {
                 exact_entry<INV>(ent, make_float2(md, mr), s_fib, s_cen, s_thr, s_sidx, s_best,
-                                 g.key + h.x, npd, at.cls);
+                                 g.key + h.x, npd, at, g.perm + h.x);
                 push = false;
             }
             if (push) {
@@ -1273,7 +1278,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
         if (tid < 32 && s_first[tid] != ~0u) {
             const unsigned q = s_first[tid] & 511u;
             exact_entry<INV>(s_q[q], s_qm[q], s_fib, s_cen, s_thr, s_sidx, s_best, g.key + h.x,
-                             npd, at.cls);
+                             npd, at, g.perm + h.x);
             s_q[q] = DONE_ENTRY;
         }
         __syncthreads();
@@ -1282,7 +1287,7 @@ k_exact_blocks(AtlasView at, GemmScratch g) {
             const unsigned ent = s_q[q];
             if (ent != DONE_ENTRY)
                 exact_entry<INV>(ent, s_qm[q], s_fib, s_cen, s_thr, s_sidx, s_best, g.key + h.x,
-                                 npd, at.cls);
+                                 npd, at, g.perm + h.x);
         }
         __syncthreads();  // the buffers are refilled for the next record
     }
@@ -1303,12 +1308,15 @@ __device__ __noinline__ void rescan_fiber(long long f, const AtlasView& at, cons
     for (int s = 0; s < at.M; ++s) {
         const float t2 = __ldg(at.thr2 + s);
         const float bound =
-            fminf(t2, key_bound2(__uint_as_float((unsigned)(g.key[f] >> 32)), at.cls));
+            pair_bound2(at, t2,
+                        key_bound2(__uint_as_float((unsigned)(g.key[f] >> 32)), at.cls));
         float d2, kf;
         int o;
         if (exact_pair(a, at.cen + (size_t)s * CROW, bound, d2, o, at.cls) &&
-            key_value(at.cls, d2, t2, ls, __ldg(at.cen + (size_t)s * CROW + NC), kf))
+            key_value(at.cls, d2, t2, ls, __ldg(at.cen + (size_t)s * CROW + NC), kf)) {
             atomicMin(g.key + f, pack_key(kf, s, o));
+            multi_mark(at, g.perm[f], at.bundle[s]);
+        }
     }
 }
 

@@ -76,7 +76,7 @@ __device__ __forceinline__ float key_best2(unsigned long long k) {
 // check costs one memory round trip; the fiber comes from shared memory.
 __device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float* fc,
                                                 const float* ls, unsigned long long* key,
-                                                unsigned e) {
+                                                unsigned e, long long f0) {
     const int c = (int)(e >> 8);
     const int f = (int)(e & 255u);
     float b[CROW];
@@ -90,12 +90,13 @@ __device__ __forceinline__ void exact_and_merge(const AtlasView& at, const float
         b[4 * q + 3] = v.w;
     }
     const float t2 = __ldg(at.thr2 + c);
-    const float bound = fminf(t2, key_bound2(key_best2(key[f]), at.cls));
+    const float bound = pair_bound2(at, t2, key_bound2(key_best2(key[f]), at.cls));
     float d2, kf;
     int o;
     // b[63] is the centroid's length (the TN term of Eq. 3)
     if (exact_pair(fc + f * NC, b, bound, d2, o, at.cls) &&
         key_value(at.cls, d2, t2, ls[f], b[CROW - 1], kf)) {
+        multi_mark(at, f0 + f, at.bundle[c]);
         const unsigned long long k = ((unsigned long long)__float_as_uint(kf) << 32) |
                                      ((unsigned long long)c << 1) | (unsigned)o;
         atomicMin(key + f, k);
@@ -267,7 +268,7 @@ __device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long l
             }
         }
         __syncwarp();
-        for (int i = lane; i < qn; i += 32) exact_and_merge(at, fc, ls, key, q[i]);
+        for (int i = lane; i < qn; i += 32) exact_and_merge(at, fc, ls, key, q[i], f0);
         __syncwarp();
         if (!full) break;
     }

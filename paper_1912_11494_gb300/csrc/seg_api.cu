@@ -354,6 +354,41 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
                       d_dist, d_cidx, d_orient, st, a->config[(int)mode], &a->prof);
 }
 
+seg_status seg_label_multi(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                           seg_mode mode, uint32_t* d_bundle_bits, int64_t words_per_fiber,
+                           int32_t* d_labels, float* d_dist, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: atlas is NULL");
+    if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: n=%lld < 0", (long long)n);
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: unknown mode %d", (int)mode);
+    const int64_t need = ((int64_t)atlas->view.B + 31) / 32;
+    if (words_per_fiber < need)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: words_per_fiber=%lld < %lld",
+                    (long long)words_per_fiber, (long long)need);
+    if (n == 0) return SEG_OK;
+    if (!d_fibers || !d_bundle_bits || !d_labels)
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: NULL fibers, bits or labels");
+    if (unaligned4(d_fibers) || unaligned4(d_bundle_bits) || unaligned4(d_labels) ||
+        unaligned4(d_dist))
+        return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: a buffer is not 4-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_bundle_bits, 0, (size_t)n * words_per_fiber * 4, st);
+    if (e) return cuda_fail(e, "seg_label_multi: clearing the bundle bits");
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    AtlasView view = atlas->view;  // this call's copy, with the multi-label output
+    view.multi = d_bundle_bits;
+    view.multi_words = words_per_fiber;
+    if (mode == SEG_MODE_PLAIN) {
+        ProfScope ps(&a->prof, PROF_PLAIN, st);
+        e = launch_label_plain(view, d_fibers, n, d_labels, d_dist, nullptr, nullptr, st,
+                               atlas->config[0]);
+        return e ? cuda_fail(e, "seg_label_multi: plain kernel") : SEG_OK;
+    }
+    return label_gemm(view, &a->gemm, &a->scratch, &a->mu, d_fibers, n, (int)mode, d_labels,
+                      d_dist, nullptr, nullptr, st, a->config[(int)mode], &a->prof);
+}
+
 seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t n,
                           seg_mode mode, int32_t* h_labels, float* h_dist, void* stream) {
     g_last_error.clear();

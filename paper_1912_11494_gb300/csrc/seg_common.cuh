@@ -75,7 +75,24 @@ struct AtlasView {
     int cls;                    // classification: 0 Eq. 2, 1 Eq. 2 + TN, 2 the paper's
                                 // direction inference + TN (seg_classification); cen[63] of
                                 // each row holds the centroid's length for the TN term
+    unsigned* multi;            // seg_label_multi: [n][multi_words] bundle bits of every
+                                // passing pair (caller's fiber order), or NULL
+    long long multi_words;
 };
+
+#ifdef __CUDACC__
+// Bound on a pair's squared point distances: theta^2 alone when every passing bundle is
+// wanted (seg_label_multi), else also the best key so far (kb2, see key_bound2).
+__device__ __forceinline__ float pair_bound2(const AtlasView& at, float t2, float kb2) {
+    return at.multi ? t2 : fminf(t2, kb2);
+}
+
+// Records a passing pair's bundle for fiber f (caller order) in the multi-label output.
+__device__ __forceinline__ void multi_mark(const AtlasView& at, long long f, int bundle) {
+    if (at.multi)
+        atomicOr(at.multi + f * at.multi_words + (bundle >> 5), 1u << (bundle & 31));
+}
+#endif
 
 // One subject of a batched call (device table; entry nsubj holds only tile0 = total tiles).
 struct BatchEntry {
