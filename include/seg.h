@@ -257,6 +257,27 @@ seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                     void* stream);
 
 /*
+ * Subject-to-atlas affine refinement driven by seg_grad (not in the paper: its subjects are
+ * registered to the atlas beforehand). Minimises
+ *     J(T) = sum over labelled fibers of d_ME(T f, c_sigma(f)) + P * (unlabelled fibers),
+ * P the atlas's largest threshold (so labelling more fibers never costs more), re-labelling
+ * every iteration: seg_apply_affine, seg_label in `mode`, seg_grad, then an Adam step in
+ * centred, radius-scaled coordinates with a learning rate of step_mm millimetres (a step
+ * moves points by about that much), halved whenever J does not improve on the best so far.
+ *   d_fibers     device float32 [n][21][3], the subject as given (n >= 1).
+ *   h_affine12   host float64 [12] in: the starting affine (A row-major, then t); out: the best
+ *                affine found.
+ *   iters >= 0, step_mm > 0.
+ *   h_cost       host float64 [iters + 1] or NULL: J at the start and after every iteration.
+ *   h_iters_done host int32 or NULL: iterations run.
+ * SYNCHRONIZES `stream` once per iteration (the 12 gradient values and J go to the host). The
+ * atlas's classification applies to the labelling; the cost is the Eq. 2 distance.
+ */
+seg_status seg_refine_affine(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                             seg_mode mode, double* h_affine12, int32_t iters, double step_mm,
+                             double* h_cost, int32_t* h_iters_done, void* stream);
+
+/*
  * seg_grad without any device allocation, for callers that cannot allocate: code running
  * inside a host allocator callback or a plugin whose host framework owns all device memory,
  * or a process whose device memory is reserved up front. The paper has no counterpart.

@@ -45,6 +45,8 @@ SIGNATURES = [
     ("seg_gemm_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    ("seg_refine_affine", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I32,
+                                         ctypes.c_double, _P, ctypes.POINTER(_I32), _P]),
     ("seg_label_multi", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P, _P, _P]),
     ("seg_resample", ctypes.c_int, [_P, _P, _I64, _P, _P]),
     ("seg_label_streamlines", ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P, _P, _P, _P,
@@ -260,6 +262,21 @@ def seg_gemm_screen_bits(atlas: Atlas, fibers, mode, stream=None):
     _check(lib().seg_gemm_screen_bits(atlas.handle, _ptr(fib), int(fib.shape[0]), m,
                                       _ptr(bits), words, _stream(stream)))
     return bits
+
+
+def seg_refine_affine(atlas: Atlas, fibers, affine12, mode="plain", iters=50, step_mm=0.5,
+                      stream=None):
+    """Refine a subject-to-atlas affine: returns (best affine float64 [12], cost history [k+1])."""
+    fib = _dev(fibers, torch.float32, "fibers").contiguous()
+    aff = (ctypes.c_double * 12)(*[float(x) for x in affine12])
+    cost = (ctypes.c_double * (int(iters) + 1))()
+    done = ctypes.c_int32()
+    _check(lib().seg_refine_affine(atlas.handle, _ptr(fib), int(fib.shape[0]), _mode(mode),
+                                   ctypes.cast(aff, ctypes.c_void_p), int(iters), float(step_mm),
+                                   ctypes.cast(cost, ctypes.c_void_p), ctypes.byref(done),
+                                   _stream(stream)))
+    import numpy as np
+    return np.array(aff[:]), np.array(cost[: done.value + 1])
 
 
 def label_multi(atlas: Atlas, fibers, mode="plain", stream=None):

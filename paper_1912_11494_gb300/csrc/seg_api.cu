@@ -136,6 +136,9 @@ struct seg_atlas {
     ScratchArena scratch{};
     ScratchArena rs_scratch{};  // seg_label_streamlines: the resampled fibers (guarded by rs_mu)
     std::mutex rs_mu;
+    ScratchArena ref_scratch{};  // seg_refine_affine's buffers (guarded by ref_mu)
+    std::mutex ref_mu;
+    float max_thr = 0.0f;        // the largest bundle threshold
     // seg_label_host: two device copies of the caller's host buffers, used by alternate calls
     // (so that a call's upload overlaps the previous call's labelling), an internal copy
     // stream, one event per chunk and one per buffer marking its last use (guarded by
@@ -182,6 +185,7 @@ static void free_atlas(seg_atlas* a) {
     free_gemm_atlas(&a->gemm);
     free_scratch(&a->scratch);
     free_scratch(&a->rs_scratch);
+    free_scratch(&a->ref_scratch);
     if (a->hcopy) cudaStreamSynchronize(a->hcopy);
     for (cudaEvent_t ev : a->hev)
         if (ev) cudaEventDestroy(ev);
@@ -264,6 +268,7 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
 
     seg_atlas* a = new seg_atlas();
     a->device = dev;
+    for (int b = 0; b < B; ++b) a->max_thr = std::max(a->max_thr, ht[b]);
     if ((e = dalloc(&a->cen, (size_t)M * CROW)) || (e = dalloc(&a->scr, M)) || (e = dalloc(&a->scr2, M_pad)) ||
         (e = dalloc(&a->thr2, M)) || (e = dalloc(&a->bundle, M)) || (e = dalloc(&a->perm, M)) ||
         (e = dalloc(&a->inv_perm, M)) || (e = dalloc(&a->status, 4))) {
@@ -605,6 +610,32 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
         return fail(SEG_ERR_INVALID_ARG, "seg_get_config: unknown mode %d", (int)mode);
     *config = atlas->config[(int)mode];
     return SEG_OK;
+}
+
+seg_status seg_refine_affine(const seg_atlas* atlas, const float* d_fibers, int64_t n,
+                             seg_mode mode, double* h_affine12, int32_t iters, double step_mm,
+                             double* h_cost, int32_t* h_iters_done, void* stream) {
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: atlas is NULL");
+    if (n <= 0 || !d_fibers || !h_affine12)
+        return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: no fibers or NULL affine");
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+        return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: unknown mode %d", (int)mode);
+    if (iters < 0 || !(step_mm > 0.0) || !std::isfinite(step_mm))
+        return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: iters=%d step=%g", iters, step_mm);
+    for (int k = 0; k < 12; ++k)
+        if (!std::isfinite(h_affine12[k]))
+            return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: non-finite affine");
+    if (unaligned4(d_fibers))
+        return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: fibers not 4-byte aligned");
+    seg_atlas* a = const_cast<seg_atlas*>(atlas);
+    int done = 0;
+    const seg_status s = refine_launch(atlas, atlas->view, &a->ref_scratch, &a->ref_mu, d_fibers,
+                                       n, (int)mode, h_affine12, iters, step_mm,
+                                       (double)atlas->max_thr, h_cost, &done,
+                                       (cudaStream_t)stream);
+    if (h_iters_done) *h_iters_done = done;
+    return s;
 }
 
 seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64_t n,

@@ -125,6 +125,10 @@ seg_status grad_noalloc_launch(const AtlasView& at, const int* inv_perm, const f
                                long long n, const double* h_aff, const int* cidx,
                                const unsigned char* orient, double* grad_aff, float* grad_cen,
                                double* cost, cudaStream_t st);
+seg_status refine_launch(const seg_atlas* atlas, const AtlasView& at, ScratchArena* scratch,
+                         std::mutex* mu, const float* fib, long long n, int mode, double* aff,
+                         int iters, double step_mm, double penalty, double* cost_out,
+                         int* iters_done, cudaStream_t st);
 seg_status resample_launch(const float* pts, const long long* off, long long n, float* out,
                            cudaStream_t st);
 seg_status apply_affine_launch(const float* in, long long n, const double* h_aff, float* out,
