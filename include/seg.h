@@ -28,6 +28,7 @@
  *  - A fiber with any non-finite coordinate gets label -1 and distance NaN.
  *  - Every entry point is safe to call from several host threads; calls on one atlas from
  *    different streams may overlap, because per-call scratch is stream-ordered.
+ *  - Every entry point opens an NVTX range named after it for the duration of the call.
  */
 #ifndef SEG_H_
 #define SEG_H_
@@ -315,6 +316,19 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
  */
 seg_status seg_set_classification(seg_atlas* atlas, seg_classification cls);
 seg_status seg_get_classification(const seg_atlas* atlas, seg_classification* cls);
+
+/*
+ * Failure-path controls (for testing error handling; not in the paper).
+ * seg_set_wait_limit: limit of the kernels' first bounded device waits, in nanoseconds (the
+ *   default is 2 s). With 0, a wait that is not complete at its first try gives up at once:
+ *   the kernel records SEG_ERR_TIMEOUT in the atlas's status word (seg_sync_status reports it),
+ *   waits (2 s at most) for its own copies and tensor-core work in flight, frees its tensor
+ *   memory and returns; the call's results are invalid, later calls are unaffected.
+ * seg_set_scratch_limit: cap, in bytes, on each of the atlas's scratch buffers (0: none); a call
+ *   that needs more returns SEG_ERR_OOM before any device work.
+ */
+seg_status seg_set_wait_limit(seg_atlas* atlas, uint64_t ns);
+seg_status seg_set_scratch_limit(seg_atlas* atlas, int64_t bytes);
 
 /*
  * Kernel timing (observability; not in the paper). While enabled on an atlas, every kernel the

@@ -52,6 +52,8 @@ SIGNATURES = [
     ("seg_label_streamlines", ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P, _P, _P, _P,
                                              _P]),
     ("seg_set_classification", ctypes.c_int, [_P, ctypes.c_int]),
+    ("seg_set_wait_limit", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("seg_set_scratch_limit", ctypes.c_int, [_P, _I64]),
     ("seg_get_classification", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("seg_gemm_screen_bits", ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P]),
     ("seg_profile_enable", ctypes.c_int, [_P, _I32]),
@@ -334,6 +336,14 @@ def seg_get_classification(atlas: Atlas) -> str:
     v = ctypes.c_int()
     _check(lib().seg_get_classification(atlas.handle, ctypes.byref(v)))
     return {i: k for k, i in CLASSIFICATIONS.items()}[v.value]
+
+
+def seg_set_wait_limit(atlas: Atlas, ns: int):
+    _check(lib().seg_set_wait_limit(atlas.handle, int(ns)))
+
+
+def seg_set_scratch_limit(atlas: Atlas, nbytes: int):
+    _check(lib().seg_set_scratch_limit(atlas.handle, int(nbytes)))
 
 
 def seg_sync_status(atlas: Atlas, stream=None):

@@ -56,6 +56,7 @@ static seg_status capture_plain(const AtlasView& at, BatchState* b, int nsubj, i
     b->total = -1;
     b->scratch_ptr = nullptr;
     b->cls = at.cls;
+    b->wait_ns = at.wait_ns;
     return SEG_OK;
 }
 
@@ -140,7 +141,7 @@ seg_status batch_launch(const AtlasView& at, GemmAtlas* g, BatchState* b, Scratc
         if (r != SEG_OK) return r;
     } else {
         if (!b->graph_exec || b->mode != SEG_MODE_PLAIN || b->nsubj != nsubj ||
-            b->config != config || b->cls != at.cls) {
+            b->config != config || b->cls != at.cls || b->wait_ns != at.wait_ns) {
             r = capture_plain(at, b, nsubj, config);
             if (r != SEG_OK) return r;
         }

@@ -97,6 +97,7 @@ struct GemmScratch {
     const int* sp_s;
     uint2* hdr;                   // [cap] {first sorted fiber, first column} or EMPTY_SLOT
     unsigned* mask;               // [cap][32] surviving columns of each of the 32 fibers
+    unsigned long long wait_ns;   // limit of the screen's bounded waits (AtlasView::wait_ns)
     unsigned long long* cnt;      // [0] records reserved, [1] fibers flagged, [2] survivors,
                                   // [3] pairs in the blocks the tensor cores computed, [4] run
                                   // counter of the exact kernel, [5] its point distances
@@ -585,10 +586,16 @@ struct GemmCfg {
 struct Waiter {
     volatile int* abort;
     unsigned* status;
+    unsigned long long limit_ns;  // 0: a wait not complete at its first try times out at once
     // wait for `parity` on `bar`; false if the CTA is aborting (another role timed out) or this
     // wait ran past its limit (then it starts the abort)
     __device__ bool wait(uint64_t* bar, uint32_t parity) const {
         if (mbar_try_wait(bar, parity)) return true;
+        if (limit_ns == 0) {
+            *abort = 1;
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
         // poll; look at the abort flag and the clock only every 1024 polls, so a completed
         // phase is seen without the latency of a timer read
         uint64_t t0 = 0;
@@ -599,7 +606,7 @@ struct Waiter {
                 const uint64_t now = globaltimer_ns();
                 if (i == 0) {
                     t0 = now;
-                } else if (now - t0 > 2000000000ull) {
+                } else if (now - t0 > limit_ns) {
                     *abort = 1;
                     atomicOr(status, ST_TIMEOUT);
                     return false;
@@ -675,7 +682,7 @@ k_gemm_screen(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const Waiter W{&s_abort, status};
+    const Waiter W{&s_abort, status, g.wait_ns};
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
@@ -1636,6 +1643,7 @@ seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     g.thr2_sp = ga->thr2_sp;
     g.sp_s = ga->sp_s;
     g.cap = cap;
+    g.wait_ns = at.wait_ns;
     c->sh = sh;
     c->n = n;
     c->n_pad = n_pad;
@@ -1763,7 +1771,8 @@ seg_status gemm_batch_launch(const AtlasView& at, GemmAtlas* ga, ScratchArena* s
     if (s != SEG_OK) return s;
     cudaError_t e = cudaSuccess;
     if (!b->graph_exec || b->mode != mode || b->config != config || b->nsubj != nsubj ||
-        b->total != total || b->scratch_ptr != c.g.a || b->cls != at.cls) {
+        b->total != total || b->scratch_ptr != c.g.a || b->cls != at.cls ||
+        b->wait_ns != at.wait_ns) {
         if (b->graph_exec) {
             cudaGraphExecDestroy((cudaGraphExec_t)b->graph_exec);
             b->graph_exec = nullptr;
@@ -1792,6 +1801,7 @@ seg_status gemm_batch_launch(const AtlasView& at, GemmAtlas* ga, ScratchArena* s
         b->total = total;
         b->scratch_ptr = c.g.a;
         b->cls = at.cls;
+        b->wait_ns = at.wait_ns;
     }
     e = cudaMemcpyAsync(b->table, host_table, table_bytes, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaEventRecord((cudaEvent_t)copied_event, st);

@@ -140,7 +140,7 @@ __device__ __forceinline__ void plain_tile(const float* __restrict__ fib, long l
     for (int c = 0; c < PC; ++c) nxt[c] = __ldg(at.scr2 + c * 32 + lane);
     (void)WS::QW;
     int ok = 1;
-    if (tma_tile && lane == 0) ok = (int)mbar_wait_bounded(bar, phase & 1u);
+    if (tma_tile && lane == 0) ok = (int)mbar_wait_bounded(bar, phase & 1u, at.wait_ns);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     if (!ok) {

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "seg_internal.cuh"
 
 namespace seg {
@@ -121,6 +123,15 @@ cudaError_t dalloc(T** p, size_t count) {
 
 using namespace seg;
 
+namespace {
+// An NVTX range around one C ABI call, so profilers show each call and the kernels it launched
+// (a no-op unless a tool is attached).
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 struct seg_atlas {
     AtlasView view{};
     int device = 0;
@@ -199,6 +210,7 @@ static void free_atlas(seg_atlas* a) {
 seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of,
                             const float* d_thresholds, int32_t M, int32_t B, int32_t npts,
                             void* stream, seg_atlas** out) {
+    const CallRange range("seg_create_atlas");
     g_last_error.clear();
     if (!out) return fail(SEG_ERR_INVALID_ARG, "seg_create_atlas: out is NULL");
     *out = nullptr;
@@ -303,6 +315,7 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
     a->view.bundle = a->bundle;
     a->view.perm = a->perm;
     a->view.status = a->status;
+    a->view.wait_ns = 2000000000ull;
     int max_per_bundle = 0;  // (cnt[b] now ends bundle b: the sort advanced it)
     for (int b = 0; b < B; ++b)
         max_per_bundle = std::max(max_per_bundle, cnt[b] - (b ? cnt[b - 1] : 0));
@@ -320,6 +333,7 @@ seg_status seg_create_atlas(const float* d_centroids, const int32_t* d_bundle_of
 }
 
 seg_status seg_destroy_atlas(seg_atlas* atlas) {
+    const CallRange range("seg_destroy_atlas");
     g_last_error.clear();
     if (!atlas) return SEG_OK;
     cudaDeviceSynchronize();
@@ -337,6 +351,7 @@ seg_status seg_atlas_info(const seg_atlas* atlas, int32_t* M, int32_t* B) {
 seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, seg_mode mode,
                      int32_t* d_labels, float* d_dist, int32_t* d_cidx, uint8_t* d_orient,
                      void* stream) {
+    const CallRange range("seg_label");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label: n=%lld < 0", (long long)n);
@@ -362,6 +377,7 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
 seg_status seg_label_multi(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                            seg_mode mode, uint32_t* d_bundle_bits, int64_t words_per_fiber,
                            int32_t* d_labels, float* d_dist, void* stream) {
+    const CallRange range("seg_label_multi");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: n=%lld < 0", (long long)n);
@@ -396,6 +412,7 @@ seg_status seg_label_multi(const seg_atlas* atlas, const float* d_fibers, int64_
 
 seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t n,
                           seg_mode mode, int32_t* h_labels, float* h_dist, void* stream) {
+    const CallRange range("seg_label_host");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_host: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_host: n=%lld < 0", (long long)n);
@@ -461,6 +478,7 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
 
 seg_status seg_resample(const float* d_points, const int64_t* d_offsets, int64_t n, float* d_out,
                         void* stream) {
+    const CallRange range("seg_resample");
     g_last_error.clear();
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_resample: n=%lld < 0", (long long)n);
     if (n == 0) return SEG_OK;
@@ -477,6 +495,7 @@ seg_status seg_label_streamlines(const seg_atlas* atlas, const float* d_points,
                                  const int64_t* d_offsets, int64_t n, seg_mode mode,
                                  int32_t* d_labels, float* d_dist, int32_t* d_cidx,
                                  uint8_t* d_orient, void* stream) {
+    const CallRange range("seg_label_streamlines");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: n < 0");
@@ -505,6 +524,7 @@ seg_status seg_label_streamlines(const seg_atlas* atlas, const float* d_points,
 seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* const* h_fibers,
                            const int64_t* h_counts, seg_mode mode, int32_t* const* h_labels,
                            float* const* h_dist, void* stream) {
+    const CallRange range("seg_label_batch");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: atlas is NULL");
     if (nsubj < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: nsubj=%d < 0", nsubj);
@@ -532,6 +552,7 @@ seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* c
 
 seg_status seg_apply_affine(const float* d_in, int64_t n, const double* h_affine12, float* d_out,
                             void* stream) {
+    const CallRange range("seg_apply_affine");
     g_last_error.clear();
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: n < 0");
     if (!h_affine12) return fail(SEG_ERR_INVALID_ARG, "seg_apply_affine: NULL affine");
@@ -546,6 +567,7 @@ seg_status seg_grad(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                     const double* h_affine12, const int32_t* d_cidx, const uint8_t* d_orient,
                     double* d_grad_affine12, float* d_grad_centroids, double* d_cost,
                     void* stream) {
+    const CallRange range("seg_grad");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_grad: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_grad: n < 0");
@@ -575,6 +597,7 @@ int32_t seg_num_configs(seg_mode mode) {
 }
 
 seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config) {
+    const CallRange range("seg_set_config");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_config: atlas is NULL");
     const int nc = seg_num_configs(mode);
@@ -586,6 +609,7 @@ seg_status seg_set_config(seg_atlas* atlas, seg_mode mode, int32_t config) {
 }
 
 seg_status seg_set_classification(seg_atlas* atlas, seg_classification cls) {
+    const CallRange range("seg_set_classification");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_classification: atlas is NULL");
     if ((int)cls < SEG_CLASS_EQ2 || (int)cls > SEG_CLASS_PAPER)
@@ -596,7 +620,28 @@ seg_status seg_set_classification(seg_atlas* atlas, seg_classification cls) {
     return SEG_OK;
 }
 
+seg_status seg_set_wait_limit(seg_atlas* atlas, uint64_t ns) {
+    const CallRange range("seg_set_wait_limit");
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_wait_limit: atlas is NULL");
+    std::lock_guard<std::mutex> lock(atlas->mu);
+    atlas->view.wait_ns = ns;
+    return SEG_OK;
+}
+
+seg_status seg_set_scratch_limit(seg_atlas* atlas, int64_t bytes) {
+    const CallRange range("seg_set_scratch_limit");
+    g_last_error.clear();
+    if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_scratch_limit: atlas is NULL");
+    if (bytes < 0) return fail(SEG_ERR_INVALID_ARG, "seg_set_scratch_limit: bytes < 0");
+    std::lock_guard<std::mutex> lock(atlas->mu);
+    for (ScratchArena* sa : {&atlas->scratch, &atlas->rs_scratch, &atlas->ref_scratch})
+        sa->limit = (size_t)bytes;
+    return SEG_OK;
+}
+
 seg_status seg_get_classification(const seg_atlas* atlas, seg_classification* cls) {
+    const CallRange range("seg_get_classification");
     g_last_error.clear();
     if (!atlas || !cls) return fail(SEG_ERR_INVALID_ARG, "seg_get_classification: NULL argument");
     *cls = (seg_classification)atlas->view.cls;
@@ -604,6 +649,7 @@ seg_status seg_get_classification(const seg_atlas* atlas, seg_classification* cl
 }
 
 seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config) {
+    const CallRange range("seg_get_config");
     g_last_error.clear();
     if (!atlas || !config) return fail(SEG_ERR_INVALID_ARG, "seg_get_config: NULL argument");
     if (seg_num_configs(mode) <= 0)
@@ -615,6 +661,7 @@ seg_status seg_get_config(const seg_atlas* atlas, seg_mode mode, int32_t* config
 seg_status seg_refine_affine(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                              seg_mode mode, double* h_affine12, int32_t iters, double step_mm,
                              double* h_cost, int32_t* h_iters_done, void* stream) {
+    const CallRange range("seg_refine_affine");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: atlas is NULL");
     if (n <= 0 || !d_fibers || !h_affine12)
@@ -642,6 +689,7 @@ seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64
                             const double* h_affine12, const int32_t* d_cidx,
                             const uint8_t* d_orient, double* d_grad_affine12,
                             float* d_grad_centroids, double* d_cost, void* stream) {
+    const CallRange range("seg_grad_noalloc");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_grad_noalloc: n < 0");
@@ -659,6 +707,7 @@ seg_status seg_grad_noalloc(const seg_atlas* atlas, const float* d_fibers, int64
 seg_status seg_gemm_screen_bits(const seg_atlas* atlas, const float* d_fibers, int64_t n,
                                 seg_mode mode, uint32_t* d_bits, int64_t words_per_fiber,
                                 void* stream) {
+    const CallRange range("seg_gemm_screen_bits");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: n < 0");
@@ -684,6 +733,7 @@ seg_status seg_gemm_screen_bits(const seg_atlas* atlas, const float* d_fibers, i
 }
 
 seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable) {
+    const CallRange range("seg_profile_enable");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_profile_enable: atlas is NULL");
     std::lock_guard<std::mutex> lock(atlas->mu);
@@ -696,6 +746,7 @@ seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable) {
 
 seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launches,
                             double* total_ms) {
+    const CallRange range("seg_profile_read");
     g_last_error.clear();
     if (!atlas || !kernel) return fail(SEG_ERR_INVALID_ARG, "seg_profile_read: NULL argument");
     static const char* names[PROF_SLOTS] = {"plain",         "batch", "gemm_prep",
@@ -723,6 +774,7 @@ seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launc
 }
 
 seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
+    const CallRange range("seg_sync_status");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_sync_status: atlas is NULL");
     cudaStream_t st = (cudaStream_t)stream;
@@ -738,6 +790,7 @@ seg_status seg_sync_status(const seg_atlas* atlas, void* stream) {
 }
 
 seg_status seg_set_gemm_record_cap(seg_atlas* atlas, int64_t records) {
+    const CallRange range("seg_set_gemm_record_cap");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_set_gemm_record_cap: atlas is NULL");
     if (records < 0)
@@ -751,6 +804,7 @@ seg_status seg_set_gemm_record_cap(seg_atlas* atlas, int64_t records) {
 seg_status seg_gemm_stats(const seg_atlas* atlas, int64_t* pairs, int64_t* survivors,
                           int64_t* overflow_fibers, int64_t* screened,
                           int64_t* point_distances) {
+    const CallRange range("seg_gemm_stats");
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_stats: atlas is NULL");
     long long h[5] = {0, 0, 0, 0, 0};

@@ -75,6 +75,8 @@ struct AtlasView {
     int cls;                    // classification: 0 Eq. 2, 1 Eq. 2 + TN, 2 the paper's
                                 // direction inference + TN (seg_classification); cen[63] of
                                 // each row holds the centroid's length for the TN term
+    unsigned long long wait_ns; // limit of the kernels' first bounded waits (default 2 s; the
+                                // drain waits after an abort always keep 2 s)
     unsigned* multi;            // seg_label_multi: [n][multi_words] bundle bits of every
                                 // passing pair (caller's fiber order), or NULL
     long long multi_words;

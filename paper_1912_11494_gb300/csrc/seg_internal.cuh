@@ -47,6 +47,7 @@ struct ScratchArena {
     void* ptr = nullptr;
     size_t bytes = 0;
     cudaEvent_t last_use = nullptr;
+    size_t limit = 0;  // the caller's cap on this arena's size (0: none); above it SEG_ERR_OOM
 };
 seg_status scratch_acquire(ScratchArena* s, size_t bytes, cudaStream_t st, void** out);
 seg_status scratch_release(ScratchArena* s, cudaStream_t st);
@@ -94,6 +95,7 @@ seg_status label_gemm(const AtlasView& at, GemmAtlas* g, ScratchArena* scratch, 
 struct BatchState {
     void* graph_exec = nullptr;   // cudaGraphExec_t
     int mode = -1, nsubj = -1, config = -1, cls = -1;
+    unsigned long long wait_ns = 0;
     long long total = -1;         // fibers of all subjects (GEMM modes: sizes the graph)
     void* scratch_ptr = nullptr;  // the scratch the GEMM graph was captured on
     void* table = nullptr;        // device BatchEntry[table_cap]

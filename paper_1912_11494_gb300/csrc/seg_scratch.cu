@@ -11,6 +11,9 @@ seg_status scratch_acquire(ScratchArena* s, size_t bytes, cudaStream_t st, void*
     } else if ((e = cudaStreamWaitEvent(st, s->last_use, 0))) {
         return cuda_fail(e, "scratch wait");
     }
+    if (s->limit && bytes > s->limit)
+        return fail(SEG_ERR_OOM, "scratch of %zu bytes exceeds the atlas's limit of %zu bytes",
+                    bytes, s->limit);
     if (bytes > s->bytes) {
         // the previous owner may still be running on another stream
         if ((e = cudaEventSynchronize(s->last_use))) return cuda_fail(e, "scratch sync");
