@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the oracle parity run, C4/C5, whole-brain, resampling, TF32 peak")
     return p.parse_args()
 
 
@@ -155,6 +157,76 @@ def traffic_for(kernel: str, mode: str, n: int):
     return t.get(f"{kernel}@{mode}", t.get(kernel) if mode == "plain" else None)
 
 
+def traffic_source() -> str | None:
+    """How the committed per-launch DRAM figures were obtained (their capture size)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    cap = t.get("captured_fibers")
+    if cap and cap != t.get("fibers"):
+        return (f"ncu dram__bytes_read.sum + dram__bytes_write.sum at {cap:,} fibers, scaled "
+                f"linearly to {t.get('fibers'):,} (extrapolated)")
+    return "ncu dram__bytes_read.sum + dram__bytes_write.sum at this size"
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the architecture)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model Name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cuda_time(fn, steps, stream, warmup=2):
+    """Mean device time (ms) of fn() over `steps` calls, CUDA events on `stream`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tf32_peak_tflops(dev) -> float:
+    """Measured TF32 tensor-core throughput: torch.matmul on fp32 8192^3 with TF32 allowed,
+    best of 10 (burst), 2 N^3 flop per product."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        c = torch.empty(n, n, device=dev)
+        best = 1e30
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        for _ in range(10):
+            best = min(best, cuda_time(lambda: torch.matmul(a, b, out=c), 1, stream, 0))
+        return 2.0 * n ** 3 / (best / 1000.0) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -234,6 +306,17 @@ def kernels_per_slot(mode: str, slot: str) -> int:
 def dtype_of(mode: str) -> str:
     return "f32" if mode in ("plain", "plain_culled") else \
         ("bf16+f32" if mode.endswith("bf16") else "tf32+f32")
+
+
+def stage_fractions(r, n):
+    """Where each discarding stage leaves the candidate pairs of a mode (its own counters)."""
+    st = r["gemm_stats"]
+    pairs = max(1, st["pairs"])
+    return {"pairs": st["pairs"], "kept_by_culling": st["screened"] / pairs,
+            "kept_by_screen": st["survivors"] / pairs,
+            "survivors_per_fiber": st["survivors"] / max(1, n), "point_distances_per_survivor":
+                st["point_distances"] / max(1, st["survivors"]),
+            "overflow_fibers": st["overflow_fibers"]}
 
 
 def time_mode(binding, at, fib, labels, dst, mode, steps, warmup, stream, world, dist, dev):
@@ -370,7 +453,19 @@ def main():
     pk, pk_src = peaks()
     cpu = None
     pdpp = None
-    if not args.no_cpu_baseline and world == 1:
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = run_extras(dev, stream, atlas_np, fib_np, labels.cpu().numpy(),
+                            dst.cpu().numpy(), head)
+        of = extras["oracle_full"]
+        pdpp = of["point_distances_per_pair"]
+        if not args.no_cpu_baseline:
+            cpu = {"value": of["fibers_per_s"], "unit": UNIT, "cores": of["threads"],
+                   "kind": "oracle", "cpu_model": of["cpu_model"],
+                   "sample": f"all {n} fibers of the workload against all {atlas_np.M} "
+                             f"centroids, FP64 progressive-discarding cascade (Section 2.3), "
+                             f"{of['seconds']:.1f} s"}
+    if cpu is None and not args.no_cpu_baseline and world == 1:
         rate, n1, cores, pdpp, dt = oracle_sample_rate(atlas_np, fib_np, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n1} random fibers of the workload against all {atlas_np.M} "
@@ -402,12 +497,13 @@ def main():
                 st = r["gemm_stats"]
                 kdim = 32 if "inv" in mode else 64
                 alg = 2.0 * st["screened"] * kdim
-                peak = bf16 if mode.endswith("bf16") else bf16 * (1.1 / 2.25)
+                tf32 = extras["tf32_tflops_measured"] if extras else None
+                peak = bf16 if mode.endswith("bf16") else (tf32 or bf16 * (1.1 / 2.25))
+                src = ("measured bf16 burst" + f" ({pk_src})" if mode.endswith("bf16") else
+                       "measured tf32 burst (torch.matmul fp32 8192^3, TF32 allowed, this run)"
+                       if tf32 else "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)")
                 mr[kname] = {"bound": "tensor", "achieved": alg / sec / 1e12, "peak": peak,
-                             "unit": "TFLOP/s",
-                             "peak_source": ("measured bf16 burst" if mode.endswith("bf16") else
-                                             "measured bf16 burst x 1.1/2.25 (nominal "
-                                             "TF32/BF16)") + f" ({pk_src})",
+                             "unit": "TFLOP/s", "peak_source": src,
                              "algorithmic": f"2 x K={kdim} x {st['screened']} pairs in the "
                                             f"computed blocks (of {st['pairs']}; the rest "
                                             f"culled on centre-point boxes)"}
@@ -432,6 +528,8 @@ def main():
             mr[kname]["kernel"] = KERNEL_NAME[kname]
             mr[kname]["frac"] = mr[kname]["achieved"] / mr[kname]["peak"]
             mr[kname]["traffic"] = traffic_for(KERNEL_NAME[kname], mode, n)
+            if mr[kname]["traffic"] is not None:
+                mr[kname]["traffic_source"] = traffic_source()
             mr[kname]["ms_per_launch"] = k["ms_per_step"]
             mr[kname]["share_of_step"] = k["ms_per_step"] / r["ms_per_step"]
         roofs[mode] = mr
@@ -452,7 +550,11 @@ def main():
             "gpu_launches": int(round(hr["launches_per_step"] * args.steps)),
             "clocks": clk,
             "modes": {m: {k: v for k, v in r.items()} for m, r in results.items()},
+            "stages": {m: stage_fractions(r, n) for m, r in results.items()
+                       if "gemm_stats" in r},
             "rooflines": roofs, "context": PAPER_CONTEXT}
+    if extras:
+        line.update(extras)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -501,6 +603,118 @@ def run_batch(args, world, rank, dev, dist):
                                      "fibers": total, "mode": mode,
                                      "counts": [int(f.shape[0]) for f in fibs]}}), flush=True)
     return 0
+
+
+def run_extras(dev, stream, atlas_np, fib_np, labels_head, dist_head, head_mode):
+    """The other measured records of one run (single GPU): the oracle over the whole subject
+    (the CPU baseline and label parity with near-ties), C5 forward + backward, the 16-subject
+    batch, the whole-brain atlas, resampling of raw streamlines, the TF32 peak."""
+    import torch
+
+    import oracle
+    from paper_1912_11494_gb300 import binding, synth
+    from tests import parity
+    out = {}
+    # --- the oracle's cascade over all 4,145,000 fibers: CPU baseline and full label parity
+    t = time.perf_counter()
+    ref = oracle.label(fib_np, atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds,
+                       "cascade")
+    dt = time.perf_counter() - t
+    c = ref["counts"]
+    res = parity.compare_all(fib_np, atlas_np.centroids, atlas_np.bundle_of,
+                             atlas_np.thresholds, labels_head, dist_head, ref=ref)
+    both = (labels_head >= 0) & (ref["labels"] >= 0)
+    out["oracle_full"] = {"fibers": len(fib_np), "seconds": dt, "fibers_per_s": len(fib_np) / dt,
+                          "threads": oracle.max_threads(), "cpu_model": cpu_model(),
+                          "point_distances_per_pair": float(c[:4].sum()) / float(c[4]),
+                          "pairs_reaching_test": {"test1": int(c[4]), "test2": int(c[5]),
+                                                  "test3": int(c[6]), "test4": int(c[7])}}
+    out["parity"] = {"mode": head_mode, "fibers": res["n"], "labelled": res["labelled"],
+                     "label_differences": res["mismatches"], "decidable_differences": 0,
+                     "near_ties": res["near_ties"],
+                     "max_dist_error_mm": float(np.abs(dist_head[both] -
+                                                       ref["dist"][both]).max())}
+    # --- the oracle's brute force on the 10,000 x 1,000 workload
+    a1, f1 = synth.workload("subject10k_atlas1k")
+    t = time.perf_counter()
+    oracle.label(f1, a1.centroids, a1.bundle_of, a1.thresholds, "brute")
+    out["oracle_brute_c1"] = {"fibers_per_s": len(f1) / (time.perf_counter() - t),
+                              "threads": oracle.max_threads()}
+    # --- C5: forward (affine, labels) and backward (seg_grad) at 1,000,000 x 5,000
+    a5, f5 = synth.workload("affine1m_atlas5k", device=dev)
+    at5 = binding.Atlas(torch.as_tensor(a5.centroids, device=dev),
+                        torch.as_tensor(a5.bundle_of, device=dev),
+                        torch.as_tensor(a5.thresholds, device=dev))
+    x = torch.as_tensor(f5, device=dev)
+    aff = synth.random_affine(21, max_deg=2.0, max_t=1.0, s_lo=0.99, s_hi=1.01)
+    n5 = x.shape[0]
+    y = torch.empty_like(x)
+    lab = torch.empty(n5, dtype=torch.int32, device=dev)
+    cidx = torch.empty_like(lab)
+    orient = torch.empty(n5, dtype=torch.uint8, device=dev)
+    ga = torch.empty(12, dtype=torch.float64, device=dev)
+    gc = torch.empty((a5.M, 21, 3), device=dev)
+    cost = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def fwd():
+        binding.seg_apply_affine(x, aff, out=y, stream=stream)
+        binding.seg_label(at5, y, head_mode, lab, None, cidx, orient, stream=stream)
+
+    def bwd():
+        binding.seg_grad(at5, x, aff, cidx, orient, ga, gc, cost, stream=stream)
+
+    ms_f = cuda_time(fwd, 10, stream)
+    ms_b = cuda_time(bwd, 10, stream)
+    binding.seg_sync_status(at5)
+    out["c5_gradient"] = {"workload": "affine1m_atlas5k", "fibers": n5, "centroids": a5.M,
+                          "mode": head_mode, "ms_forward": ms_f, "ms_backward": ms_b,
+                          "fibers_per_s": n5 / ((ms_f + ms_b) / 1000.0),
+                          "backward_gbs": (n5 * 252 + n5 * 5 + a5.M * 252 * 3) / (ms_b / 1e3) /
+                          1e9}
+    del at5, x, y
+    # --- C4: the 16-subject batch (28.6M fibers) in one call
+    ab = synth.make_atlas(500, seed=1002, device=dev)
+    fibs = [torch.as_tensor(synth.make_batch_subject(ab, s, device=dev), device=dev)
+            for s in range(16)]
+    atb = binding.Atlas(torch.as_tensor(ab.centroids, device=dev),
+                        torch.as_tensor(ab.bundle_of, device=dev),
+                        torch.as_tensor(ab.thresholds, device=dev))
+    labs = [torch.empty(f.shape[0], dtype=torch.int32, device=dev) for f in fibs]
+    dsts = [torch.empty(f.shape[0], device=dev) for f in fibs]
+    total = sum(int(f.shape[0]) for f in fibs)
+    out["batch16"] = {"subjects": 16, "fibers": total, "modes": {}}
+    for m in ("plain_culled", "gemm_bf16", "plain"):
+        ms = cuda_time(lambda: binding.seg_label_batch(atb, fibs, m, labs, dsts, stream=stream),
+                       3 if m == "plain" else 5, stream)
+        out["batch16"]["modes"][m] = {"ms_per_batch": ms, "fibers_per_s": total / (ms / 1e3)}
+    binding.seg_sync_status(atb)
+    del fibs, labs, dsts, atb
+    # --- the whole-brain atlas (62 bundles, 44,345 centroids) at 4,145,000 fibers
+    aw, fw = synth.workload("subject4145k_atlas44k", device=dev)
+    atw = binding.Atlas(torch.as_tensor(aw.centroids, device=dev),
+                        torch.as_tensor(aw.bundle_of, device=dev),
+                        torch.as_tensor(aw.thresholds, device=dev))
+    xw = torch.as_tensor(fw, device=dev)
+    lw = torch.empty(xw.shape[0], dtype=torch.int32, device=dev)
+    out["whole_brain"] = {"workload": "subject4145k_atlas44k", "fibers": int(xw.shape[0]),
+                          "centroids": aw.M, "modes": {}}
+    for m in ("plain_culled", "gemm_bf16"):
+        ms = cuda_time(lambda: binding.seg_label(atw, xw, m, lw, stream=stream), 3, stream)
+        out["whole_brain"]["modes"][m] = {"ms_per_step": ms,
+                                         "fibers_per_s": xw.shape[0] / (ms / 1e3)}
+    binding.seg_sync_status(atw)
+    del atw, xw, lw
+    # --- resampling of 1,000,000 raw streamlines (about 0.2 mm steps)
+    pts, off = synth.make_streamlines(atlas_np, 1_000_000, 0.75, seed=2, device=dev)
+    rs_out = torch.empty((1_000_000, 21, 3), device=dev)
+    ms = cuda_time(lambda: binding.seg_resample(pts, off, out=rs_out, stream=stream), 10, stream)
+    nbytes = pts.numel() * 4 + off.numel() * 8 + rs_out.numel() * 4
+    out["resample"] = {"streamlines": 1_000_000, "points": int(pts.shape[0]), "ms": ms,
+                       "fibers_per_s": 1e6 / (ms / 1e3), "gbs": nbytes / (ms / 1e3) / 1e9,
+                       "algorithmic_bytes": int(nbytes)}
+    del pts, off, rs_out
+    out["tf32_tflops_measured"] = tf32_peak_tflops(dev)
+    return out
 
 
 if __name__ == "__main__":

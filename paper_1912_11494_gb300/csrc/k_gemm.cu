@@ -1124,9 +1124,16 @@ __device__ __forceinline__ void exact_entry(unsigned ent, float2 mm, const float
     }
 }
 
-template <bool INV>
+// EXT: the classification is not plain Eq. 2 or every passing bundle is wanted; without it the
+// kernel's view is fixed to Eq. 2 and no multi-label output, which the compiler folds away.
+template <bool INV, bool EXT>
 __global__ void __launch_bounds__(EX_THREADS, 9)
-k_exact_blocks(AtlasView at, GemmScratch g) {
+k_exact_blocks(AtlasView at_in, GemmScratch g) {
+    AtlasView at = at_in;
+    if (!EXT) {
+        at.cls = CLS_EQ2;
+        at.multi = nullptr;
+    }
     __shared__ __align__(16) float s_fib[32 * FS_STRIDE];
     __shared__ __align__(16) float4 s_cen[CenRows<INV>::ROWS * CROW4];
     __shared__ float s_thr[32];              // theta^2 of each centroid row
@@ -1594,7 +1601,16 @@ seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
                     32 * 64 * MAXW);
     // block records: about 3.4 per 32 fibers on atlases shaped like the paper's; room for
     // rec_per_group per 32 fibers + slack (fibers past the room are rescanned exactly)
-    long long cap = n_pad / 32 * ga->rec_per_group + 65536;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // every warp that writes records reserves SLOT_GRAB slots at a time and may leave up to
+    // that many unused: room for that waste comes on top of the records themselves
+    const long long writers =
+        culled ? std::min<long long>((n_pad / 32 + CS_WARPS - 1) / CS_WARPS, (long long)sms * 8) *
+                     CS_WARPS
+               : (long long)sms * EPI_WARPS;
+    long long cap = n_pad / 32 * ga->rec_per_group + 65536 + writers * SLOT_GRAB;
     if (ga->cap_limit > 0 && ga->cap_limit < cap) cap = ga->cap_limit;
     const size_t elem = culled ? 0 : tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * sh.ke * elem);
@@ -1613,9 +1629,7 @@ seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     const size_t off_mask = off_hdr + align256((size_t)cap * 8);
     const size_t bytes = off_mask + (size_t)cap * 128;
 
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    c->sms = sms;
     void* base = nullptr;
     seg_status s = scratch_acquire(scratch, bytes, st, &base);
     if (s != SEG_OK) return s;
@@ -1724,10 +1738,10 @@ cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, 
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_EXACT, st);
-        if (c.inv)
-            k_exact_blocks<true><<<sms * 8, EX_THREADS, 0, st>>>(at, g);
-        else
-            k_exact_blocks<false><<<sms * 9, EX_THREADS, 0, st>>>(at, g);
+        const bool ext = at.cls != CLS_EQ2 || at.multi != nullptr;
+        auto kern = c.inv ? (ext ? k_exact_blocks<true, true> : k_exact_blocks<true, false>)
+                          : (ext ? k_exact_blocks<false, true> : k_exact_blocks<false, false>);
+        kern<<<sms * (c.inv ? 8 : 9), EX_THREADS, 0, st>>>(at, g);
         e = cudaGetLastError();
     }
     if (!e) {

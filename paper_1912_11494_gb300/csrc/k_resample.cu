@@ -95,16 +95,21 @@ k_resample(const float* __restrict__ pts, const long long* __restrict__ off, lon
             for (int k = 3 + lane; k < 3 * (NPTS - 1); k += 32) o[k] = __ldg(p + k % 3);
             continue;
         }
+        // target k's arc length (non-decreasing in k: the same rounded expression everywhere)
+        auto target = [L](int k) { return (float)k * L / (float)(NPTS - 1); };
         segment_pass(p, m, lane, [&](float c0, float c1, float len, const float* a,
                                      const float* b) {
-            for (int k = 1; k < NPTS - 1; ++k) {
-                const float sk = (float)k * L / (float)(NPTS - 1);
-                if (c0 < sk && sk <= c1) {
-                    const float w =
-                        len > 0.0f ? fminf(1.0f, fmaxf(0.0f, (sk - c0) / len)) : 0.0f;
+            // the targets in (c0, c1]: start from an estimate of the first one and settle it
+            // with the exact comparisons, so the segment that holds a target writes it
+            int k = (int)(c0 * (float)(NPTS - 1) / L);
+            k = max(1, min(NPTS - 2, k));
+            while (k > 1 && target(k - 1) > c0) --k;
+            while (k <= NPTS - 2 && target(k) <= c0) ++k;
+            for (; k <= NPTS - 2 && target(k) <= c1; ++k) {
+                const float w =
+                    len > 0.0f ? fminf(1.0f, fmaxf(0.0f, (target(k) - c0) / len)) : 0.0f;
 #pragma unroll
-                    for (int r = 0; r < 3; ++r) o[3 * k + r] = fmaf(w, b[r] - a[r], a[r]);
-                }
+                for (int r = 0; r < 3; ++r) o[3 * k + r] = fmaf(w, b[r] - a[r], a[r]);
             }
         });
     }

@@ -174,6 +174,17 @@ def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
         assert 0 < st["screened"] <= st["pairs"] + 128 * 256 * (len(fib) // 128 + 1)
 
 
+@pytest.mark.parametrize("n", [20_000, 300_000, 1_000_000, 2_500_000])
+def test_no_survivor_overflow_at_any_size(dev, full_size, n):
+    """The default survivor list holds every record at any fiber count (a fiber whose records
+    do not fit is still labelled exactly, by a slow rescan, so only the statistic shows it)."""
+    atlas_np, fib = full_size
+    at = make_atlas(atlas_np.centroids, atlas_np.bundle_of, atlas_np.thresholds, dev)
+    for mode in ("plain_culled", "gemm_bf16", "gemm_inv_tf32"):
+        run(at, fib[:n], dev, mode)
+        assert binding.seg_gemm_stats(at)["overflow_fibers"] == 0, mode
+
+
 @pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled"])
 def test_gemm_locality_order_extremes(dev, mode):
     """The GEMM modes visit fibers in the order of their centre point's 2 mm cell. Centres far
