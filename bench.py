@@ -374,6 +374,8 @@ def main():
     build.build()
     if args.workload.startswith("batch"):
         return run_batch(args, world, rank, dev, dist)
+    if args.workload.startswith("streamlines"):
+        return run_streamlines(args, world, rank, dev, dist)
 
     atlas_np, fib_np = synth.workload(args.workload, n=args.n, device=dev)
     n = int(fib_np.shape[0])
@@ -602,6 +604,48 @@ def run_batch(args, world, rank, dev, dist):
                           "config": {"workload": args.workload, "subjects": 16,
                                      "fibers": total, "mode": mode,
                                      "counts": [int(f.shape[0]) for f in fibs]}}), flush=True)
+    return 0
+
+
+def run_streamlines(args, world, rank, dev, dist):
+    """Raw tractography in, labels out: 1,000,000 streamlines of the subject recipe (about
+    0.2 mm steps) against the 500 x 20 atlas, resampled to 21 points (seg_resample) and labelled
+    (seg_label_streamlines, which resamples and labels)."""
+    import torch
+
+    from paper_1912_11494_gb300 import binding, synth
+    n = args.n or 1_000_000
+    atlas_np = synth.make_atlas(500, seed=1002, device=dev)
+    pts, off = synth.make_streamlines(atlas_np, n, 0.75, seed=2, device=dev)
+    at = binding.Atlas(torch.as_tensor(atlas_np.centroids, device=dev),
+                       torch.as_tensor(atlas_np.bundle_of, device=dev),
+                       torch.as_tensor(atlas_np.thresholds, device=dev))
+    mode = "plain_culled" if args.mode == "best" else args.mode
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((n, 21, 3), device=dev)
+    ms_rs = cuda_time(lambda: binding.seg_resample(pts, off, out=out, stream=stream), args.steps,
+                      stream, max(3, args.warmup))
+    ms_all = cuda_time(lambda: binding.label_streamlines(at, pts, off, mode, stream=stream),
+                       args.steps, stream, max(3, args.warmup))
+    binding.seg_sync_status(at)
+    nbytes = pts.numel() * 4 + off.numel() * 8 + out.numel() * 4
+    pk, _ = peaks()
+    if rank == 0:
+        print(json.dumps({"metric": "raw streamlines resampled and labelled/sec",
+                          "value": world * n / (ms_all / 1000.0), "unit": "streamlines/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+                          "dtype": dtype_of(mode), "data": "synthetic",
+                          "config": {"workload": args.workload, "streamlines": n,
+                                     "points": int(pts.shape[0]), "mode": mode},
+                          "resample": {"ms": ms_rs, "streamlines_per_s": n / (ms_rs / 1e3),
+                                       "roofline": {"bound": "hbm",
+                                                    "achieved": nbytes / (ms_rs / 1e3) / 1e9,
+                                                    "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                                    "frac": nbytes / (ms_rs / 1e3) / 1e9 /
+                                                    pk["hbm_gbs"],
+                                                    "algorithmic_bytes": int(nbytes)}}}),
+              flush=True)
     return 0
 
 

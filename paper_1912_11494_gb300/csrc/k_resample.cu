@@ -95,13 +95,15 @@ k_resample(const float* __restrict__ pts, const long long* __restrict__ off, lon
             for (int k = 3 + lane; k < 3 * (NPTS - 1); k += 32) o[k] = __ldg(p + k % 3);
             continue;
         }
-        // target k's arc length (non-decreasing in k: the same rounded expression everywhere)
-        auto target = [L](int k) { return (float)k * L / (float)(NPTS - 1); };
+        // target k's arc length, k L / 20 as k times the rounded L / 20 (non-decreasing in k,
+        // below L for k <= 19, and the same expression wherever it is compared)
+        const float step = L / (float)(NPTS - 1), inv = 1.0f / step;
+        auto target = [step](int k) { return (float)k * step; };
         segment_pass(p, m, lane, [&](float c0, float c1, float len, const float* a,
                                      const float* b) {
             // the targets in (c0, c1]: start from an estimate of the first one and settle it
             // with the exact comparisons, so the segment that holds a target writes it
-            int k = (int)(c0 * (float)(NPTS - 1) / L);
+            int k = (int)(c0 * inv);
             k = max(1, min(NPTS - 2, k));
             while (k > 1 && target(k - 1) > c0) --k;
             while (k <= NPTS - 2 && target(k) <= c0) ++k;
