@@ -23,6 +23,12 @@ def test_traffic_only_for_the_captured_instantiation_and_size():
     assert bench.traffic_for("k_label_plain", "plain", 1_000_000) is None
 
 
+def test_traffic_is_marked_with_its_capture_size():
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    assert t["captured_fibers"] == 1_000_000
+    assert "extrapolated" in bench.traffic_source() and "1,000,000" in bench.traffic_source()
+
+
 def test_profiled_scopes_exist_in_the_library():
     for slot in bench.LAUNCH_SLOTS:
         assert slot in binding.PROFILED_KERNELS
@@ -36,7 +42,7 @@ def test_every_traffic_figure_has_its_ncu_summary():
     texts = [open(os.path.join(ROOT, "profiles", f)).read()
              for f in os.listdir(os.path.join(ROOT, "profiles")) if f.endswith(".md")]
     for key in t:
-        if key.startswith("_") or key == "fibers":
+        if key.startswith("_") or key in ("fibers", "captured_fibers"):
             continue
         kernel = key.split("@")[0]
         assert any(kernel in x and "dram__bytes_read.sum" in x for x in texts), key
