@@ -284,18 +284,20 @@ def _has_cuda():
 
 
 # ----------------------------------------------------------------------------- our arm
-MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled")
+MODES = ("plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled",
+         "culled_fused")
 KERNEL_NAME = {"plain": "k_label_plain", "gemm_screen": "k_gemm_screen",
-               "cull_screen": "k_culled_screen",
+               "cull_screen": "k_culled_screen", "culled_fused": "k_fused",
                "gemm_exact": "k_exact_blocks", "gemm_prep": "k_prep_a",
                "gemm_sort": "k_bin_count", "gemm_finalize": "k_finalize"}
-LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "cull_screen", "gemm_exact",
-                "gemm_finalize")
+LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "cull_screen", "culled_fused",
+                "gemm_exact", "gemm_finalize")
 # kernels the library launches inside each profiled scope (the sort is a count, two scans and a
 # scatter; the prep scope holds the fiber operand, the tile boxes and the active-block masks;
 # the finalize scope the overflow rescan and the label write)
 KERNELS_PER_SLOT = {"plain": 1, "gemm_sort": 4, "gemm_prep": 3, "gemm_screen": 1,
-                    "cull_screen": 1, "gemm_exact": 1, "gemm_finalize": 2}
+                    "cull_screen": 1, "gemm_exact": 1, "gemm_finalize": 2,
+                    "culled_fused": 3}
 
 
 def kernels_per_slot(mode: str, slot: str) -> int:
@@ -304,7 +306,7 @@ def kernels_per_slot(mode: str, slot: str) -> int:
 
 
 def dtype_of(mode: str) -> str:
-    return "f32" if mode in ("plain", "plain_culled") else \
+    return "f32" if mode in ("plain", "plain_culled", "culled_fused") else \
         ("bf16+f32" if mode.endswith("bf16") else "tf32+f32")
 
 
@@ -517,6 +519,15 @@ def main():
                              "algorithmic": f"test1 in dot-product form (3 FMA = 6 flop) x "
                                             f"{st['screened']} pairs in the blocks kept by the "
                                             f"centre-point culling (of {st['pairs']})"}
+            elif kname == "culled_fused":
+                st = r["gemm_stats"]
+                alg = 6.0 * st["screened"] + 8.0 * st["point_distances"]
+                mr[kname] = {"bound": "alu", "achieved": alg / sec / 1e12, "peak": alu_peak,
+                             "unit": "TFLOP/s", "peak_source": alu_src,
+                             "algorithmic": f"test1 in dot-product form (6 flop) x "
+                                            f"{st['screened']} pairs in the blocks kept by the "
+                                            f"culling + {st['point_distances']} squared point "
+                                            f"distances of the exact test x 8 flop"}
             elif kname == "gemm_exact":
                 st = r["gemm_stats"]
                 alg = 8.0 * st["point_distances"]

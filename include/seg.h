@@ -82,7 +82,14 @@ typedef enum {
      * test (both orientations) on the pairs that pass. Labels and distances equal
      * SEG_MODE_PLAIN's. The culling is not in the paper (its Section 2.4 "data locality" is a
      * cache argument); it is reported as its own algorithmic mode. */
-    SEG_MODE_PLAIN_CULLED = 5
+    SEG_MODE_PLAIN_CULLED = 5,
+    /* SEG_MODE_PLAIN_CULLED's work in one kernel after the locality sort: a warp takes a
+     * 32-fiber group, stages its rows once, culls the 32-centroid chunks by centre-point box,
+     * runs test1 on the chunks in reach and the exact test (both orientations) on their
+     * survivors at once, and keeps each fiber's best in on-chip memory. No survivor list, so
+     * no list capacity and no overflow path. Labels and distances equal SEG_MODE_PLAIN's. Not
+     * in the paper. seg_gemm_screen_bits does not take this mode (it has no separate screen). */
+    SEG_MODE_CULLED_FUSED = 6
 } seg_mode;
 
 typedef struct seg_atlas seg_atlas; /* opaque; owns its device copies of the atlas */
@@ -211,7 +218,7 @@ seg_status seg_label_streamlines(const seg_atlas* atlas, const float* d_points,
  * and writes h_labels[s] (required) and h_dist[s] (array or entries may be NULL). The pointer
  * arrays are host memory read during the call. Results per subject equal seg_label's.
  *  - SEG_MODE_PLAIN: one persistent launch over (subject, 32-fiber tile) work items.
- *  - GEMM modes and SEG_MODE_PLAIN_CULLED: the subjects form one virtual array of fibers that
+ *  - GEMM modes, SEG_MODE_PLAIN_CULLED and SEG_MODE_CULLED_FUSED: the subjects form one virtual array of fibers that
  *    goes through the mode's launch sequence once (sorted and screened together).
  * In every mode the launches are captured once into a CUDA graph and replayed; the graph is
  * captured again when the mode, tile shape or subject count changes (and, in the GEMM and
@@ -336,7 +343,8 @@ seg_status seg_set_scratch_limit(seg_atlas* atlas, int64_t bytes);
  * seg_profile_read waits for those events and returns, for one kernel name, the number of
  * launches and their summed duration in milliseconds since profiling was (re)enabled.
  * Kernel names: "plain", "batch", "gemm_sort", "gemm_prep" (their launches precede the
- * screen), "gemm_screen", "cull_screen" (SEG_MODE_PLAIN_CULLED's test1 screen), "gemm_exact",
+ * screen), "gemm_screen", "cull_screen" (SEG_MODE_PLAIN_CULLED's test1 screen), "culled_fused"
+ * (SEG_MODE_CULLED_FUSED's one kernel after the sort), "gemm_exact",
  * "gemm_finalize", "grad". Enabling (or disabling) clears what was recorded.
  */
 seg_status seg_profile_enable(seg_atlas* atlas, int32_t enable);

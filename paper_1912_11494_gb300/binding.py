@@ -18,7 +18,7 @@ SEG_OK = 0
 STATUS_NAMES = {0: "SEG_OK", 1: "SEG_ERR_INVALID_ARG", 2: "SEG_ERR_CUDA", 3: "SEG_ERR_OOM",
                 4: "SEG_ERR_UNSUPPORTED", 5: "SEG_ERR_TIMEOUT", 6: "SEG_ERR_OVERFLOW"}
 MODES = {"plain": 0, "gemm_bf16": 1, "gemm_tf32": 2, "gemm_inv_bf16": 3, "gemm_inv_tf32": 4,
-         "plain_culled": 5}
+         "plain_culled": 5, "culled_fused": 6}
 NPTS = 21
 
 # Every entry point the header declares: (name, restype, argtypes).
@@ -363,7 +363,7 @@ def seg_gemm_stats(atlas: Atlas):
 
 
 PROFILED_KERNELS = ("plain", "batch", "gemm_sort", "gemm_prep", "gemm_screen", "cull_screen",
-                    "gemm_exact", "gemm_finalize", "grad")
+                    "gemm_exact", "gemm_finalize", "grad", "culled_fused")
 
 
 def seg_profile_enable(atlas: Atlas, enable: bool = True):

@@ -93,6 +93,7 @@ struct GemmScratch {
                                       // chunks may; the epilogue reads only those chunks)
     int awords;
     const float4* cen_sp;         // the atlas's spatial-order arrays (GemmAtlas)
+    const float4* end_sp;
     const float* thr2_sp;
     const int* sp_s;
     uint2* hdr;                   // [cap] {first sorted fiber, first column} or EMPTY_SLOT
@@ -537,9 +538,13 @@ __global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, in
 // Spatial-order copies of the atlas for the GEMM modes (centroid rows point-major: point i as
 // the float4 (x, y, z, 0), CROW4 per row).
 __global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float4* cen_sp,
-                               float* thr2_sp, float4* ctr_sp, float4* scr_sp) {
+                               float* thr2_sp, float4* ctr_sp, float4* scr_sp, float4* end_sp) {
     const int c = blockIdx.x * blockDim.y + threadIdx.y;
-    if (c >= at.M) return;
+    if (c >= at.M) {  // scr_sp's pad up to a whole chunk: a row no fiber passes
+        if (c < (at.M + 31) / 32 * 32 && threadIdx.x == 0)
+            scr_sp[c] = make_float4(0.0f, 0.0f, 0.0f, -INFINITY);
+        return;
+    }
     const int s = sp_s[c];
     const float* src = at.cen + (size_t)s * CROW;
     for (int k = threadIdx.x; k < CROW4; k += blockDim.x)
@@ -552,6 +557,10 @@ __global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float
         scr_sp[c] = at.scr2[s];
         ctr_sp[c] = make_float4(src[3 * CENTRE], src[3 * CENTRE + 1], src[3 * CENTRE + 2],
                                 at.thr2[s]);
+        end_sp[3 * (size_t)c] = make_float4(src[0], src[1], src[2], src[CROW - 1]);
+        end_sp[3 * (size_t)c + 1] = ctr_sp[c];
+        const int L = 3 * (NPTS - 1);
+        end_sp[3 * (size_t)c + 2] = make_float4(src[L], src[L + 1], src[L + 2], 0.0f);
     }
 }
 
@@ -1077,6 +1086,300 @@ __device__ __forceinline__ float rest17(const float* a, const float4* b, float m
     return m;
 }
 
+// ---- SEG_MODE_CULLED_FUSED: culling, test1 and the exact test in one pass per fiber group -----
+// One warp owns a 32-fiber group of the locality order from start to finish: it gathers the
+// group's 32 rows from the caller's array into shared memory once (odd row stride, so lanes
+// reading different rows at one column never share a bank), tests the group's centre-point box
+// against the 32-centroid chunks (a ballot over 32 chunks at a time), runs test1 in dot-product
+// form for every pair of a chunk in reach (the chunk's 32 screen rows read as broadcasts), and
+// runs the exact test (Section 2.3: test1..test4, both orientations, early exits) on that
+// chunk's survivors at once: 32 pairs per round in column-major order (the rows' masks
+// transposed by ballots), so the lanes of a round mostly read the same centroid row (L1
+// broadcasts) while each reads its own fiber's points from shared memory. Each fiber's packed
+// key and best value live in shared memory (atomicMin), so there is no sorted copy, no record
+// list and no overflow path; the bound tightens as the chunks are visited in spatial order.
+constexpr int FZ_WARPS = 4;
+constexpr int FZ_CTAS = 5;         // resident CTAs per SM (96 registers a thread)
+constexpr int FZ_STRIDE = NC + 2;  // 65 floats per fiber row in shared memory (odd)
+
+constexpr int FZ_QLEN = 64;  // queued pairs per warp: fewer than 32 wait, plus one round
+constexpr int FZ_MAX_M = 1 << 25;  // a queued pair packs the centroid index in 25 bits
+
+// 9,856 bytes a warp: five 4-warp CTAs an SM (with the 80 registers a thread that six would
+// leave, and test1's rows read through L1, the kernel is slower).
+struct FzWarp {
+    float f[32 * FZ_STRIDE];   // the group's fiber rows (column 63: the fiber's length, for TN)
+    float4 q[32];              // the current chunk's test1 rows
+    unsigned long long key[32];  // packed keys; the high word is the fiber's best value so far
+    float2 qm[FZ_QLEN];        // queued pairs: partial maxima after test2 (direct, reversed)
+    unsigned qe[FZ_QLEN];      //   fiber | live direct << 5 | live reversed << 6 | centroid << 7
+};
+
+// A fiber's best key value so far (the float bits in its key's high word; all ones when none).
+__device__ __forceinline__ float fz_best(const FzWarp& S, int fl) {
+    return __uint_as_float(reinterpret_cast<const unsigned*>(S.key)[2 * fl + 1]);
+}
+
+// Phase A of a pair: test1 and test2 (centre and end points) of fiber a (shared, 63 floats)
+// against the centroid's points 0, 10, 20, both orientations (the one the end points infer with
+// cls == CLS_PAPER). The same arithmetic as the exact kernel's. Returns the live orientations (bit 0 direct, bit 1
+// reversed) and their partial maxima.
+__device__ __forceinline__ float pd2q(const float* a, int i, float4 q) {
+    const float dx = a[3 * i] - q.x;
+    const float dy = a[3 * i + 1] - q.y;
+    const float dz = a[3 * i + 2] - q.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+__device__ __forceinline__ unsigned fz_phase_a(const float* a, float4 q0, float4 q10, float4 q20,
+                                               float bound, int cls, float& md, float& mr,
+                                               unsigned& npd) {
+    constexpr int L = NPTS - 1;
+    const float c = pd2q(a, CENTRE, q10);
+    npd += 1;
+    if (!(c <= bound)) return 0u;
+    md = fmaxf(c, fmaxf(pd2q(a, 0, q0), pd2q(a, L, q20)));
+    mr = fmaxf(c, fmaxf(pd2q(a, 0, q20), pd2q(a, L, q0)));
+    npd += 4;
+    bool ad = md <= bound, ar = mr <= bound;
+    if (cls == CLS_PAPER) {  // direction inferred from the end points
+        const bool direct = md <= mr;
+        ad = ad && direct;
+        ar = ar && !direct;
+    }
+    return (ad ? 1u : 0u) | (ar ? 2u : 0u);
+}
+
+// Phase B of a queued pair: test3 and test4 in its live orientations against min(theta^2, the
+// fiber's best so far), then the merge into the fiber's key and best (Algorithm 1's tie rule:
+// exits are strict, so equal values still reach the atomicMin of the packed key).
+template <bool EXT>
+__device__ __forceinline__ void fz_phase_b(FzWarp& S, int e, const AtlasView& at,
+                                           const GemmScratch& g, const unsigned* perm,
+                                           long long f0, unsigned& npd) {
+    const unsigned fl_bits = S.qe[e];
+    const int fl = (int)(fl_bits & 31u), j = (int)(fl_bits >> 7);
+    const float2 mm = S.qm[e];
+    const float* a = S.f + fl * FZ_STRIDE;
+    const float4* b = g.cen_sp + (size_t)j * CROW4;
+    const float t2 = __ldg(g.thr2_sp + j);
+    const float bound = pair_bound2(at, t2, key_bound2(fz_best(S, fl), at.cls));
+    float md = mm.x, mr = mm.y;
+    bool ad = ((fl_bits >> 5) & 1u) && md <= bound;
+    bool ar = ((fl_bits >> 6) & 1u) && mr <= bound;
+    if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; npd += 4; }
+    if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; npd += 4; }
+    if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; npd += 14; }
+    if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; npd += 14; }
+    if (!(ad || ar)) return;
+    const bool dir = ad && (!ar || md <= mr);
+    const float d2 = dir ? md : mr;
+    float kf;
+    if (key_value(at.cls, d2, t2, a[NC], __ldg(&b[0].w), kf)) {
+        const int sidx = __ldg(g.sp_s + j);
+        atomicMin(&S.key[fl], pack_key(kf, sidx, dir ? 0 : 1));
+        if (EXT && at.multi) multi_mark(at, perm[f0 + fl], at.bundle[sidx]);
+    }
+}
+
+template <bool EXT>
+__global__ void __launch_bounds__(FZ_WARPS * 32, FZ_CTAS)
+k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long n_groups,
+        AtlasView at_in, GemmScratch g, const float4* __restrict__ scr_sp,
+        const float4* __restrict__ tbox, int n_chunks, int* labels, float* dist, int* cidx,
+        unsigned char* orient) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    AtlasView at = at_in;
+    if (!EXT) {
+        at.cls = CLS_EQ2;
+        at.multi = nullptr;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    FzWarp& S = reinterpret_cast<FzWarp*>(fz_smem)[w];
+    unsigned long long screened = 0, surv = 0;
+    unsigned npd = 0;
+    const long long W = (long long)gridDim.x * FZ_WARPS;
+    for (long long grp = (long long)blockIdx.x * FZ_WARPS + w; grp < n_groups; grp += W) {
+        const long long f0 = grp * 32;
+        const int rows_in = (int)max(0LL, min(32LL, n - f0));
+        int qn = 0;  // queued pairs (warp-uniform)
+        // 1. the group's rows (all copies in flight together)
+        const unsigned my_src = lane < rows_in ? __ldg(perm + f0 + lane) : 0u;
+        __syncwarp();
+        for (int r = 0; r < rows_in; ++r) {
+            const float* p = src.row(__shfl_sync(0xffffffffu, my_src, r));
+            cp_async4(S.f + r * FZ_STRIDE + lane, p + lane);
+            if (lane < NC - 32) cp_async4(S.f + r * FZ_STRIDE + 32 + lane, p + 32 + lane);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        // 2. this lane's fiber: screen values, key, length; the group's centre-point box
+        const float* a = S.f + lane * FZ_STRIDE;
+        bool finite = lane < rows_in;  // every centred coordinate finite, as in the other modes
+        for (int k = 0; k < NC && finite; k += 3)
+            finite = isfinite(a[k] - at.c0x) && isfinite(a[k + 1] - at.c0y) &&
+                     isfinite(a[k + 2] - at.c0z);
+        float x = 0.f, y = 0.f, z = 0.f, h = NAN;  // NaN never passes test1
+        if (finite) {
+            x = a[3 * CENTRE] - at.c0x;
+            y = a[3 * CENTRE + 1] - at.c0y;
+            z = a[3 * CENTRE + 2] - at.c0z;
+            const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+            h = 0.5f * r2 - 1e-5f * r2 - 1e-3f;
+        }
+        S.key[lane] = finite ? ~0ull : NAN_KEY;
+        S.f[lane * FZ_STRIDE + NC] = at.cls != CLS_EQ2 && finite ? poly_length(a) : 0.0f;
+        UnitBox box;
+        {
+            float lo[3], hi[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float c = finite ? a[3 * CENTRE + r] : 0.0f;
+                lo[r] = finite ? c : INFINITY;
+                hi[r] = finite ? c : -INFINITY;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    lo[r] = fminf(lo[r], __shfl_xor_sync(0xffffffffu, lo[r], off));
+                    hi[r] = fmaxf(hi[r], __shfl_xor_sync(0xffffffffu, hi[r], off));
+                }
+            }
+            box = UnitBox{lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+        }
+        __syncwarp();
+        // 3. the chunks in reach
+        for (int k0 = 0; box.lx <= box.hx && k0 < n_chunks; k0 += 32) {
+            const int cq = k0 + lane;
+            unsigned act = __ballot_sync(0xffffffffu, cq < n_chunks && block_active(box, tbox, cq));
+            while (act) {
+                const int cc = k0 + __ffs(act) - 1;
+                act &= act - 1;
+                S.q[lane] = __ldg(scr_sp + 32 * (size_t)cc + lane);  // padded to whole chunks
+                __syncwarp();
+                unsigned m = 0u;  // test1 (dot-product form with its slack) of this lane's fiber
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float4 q = S.q[i];  // the same row for every lane: a broadcast
+                    const float t = fmaf(z, q.z, fmaf(y, q.y, fmaf(x, q.x, q.w)));
+                    m |= (t >= h ? 1u : 0u) << i;
+                }
+                screened += 32;
+                __syncwarp();
+                if (!__any_sync(0xffffffffu, m != 0u)) continue;
+                surv += __popc(m);
+                unsigned cm = 0u;  // lane b: the fibers whose centroid b passed test1
+#pragma unroll
+                for (int bb = 0; bb < 32; ++bb) {
+                    const unsigned v = __ballot_sync(0xffffffffu, (m >> bb) & 1u);
+                    if (lane == bb) cm = v;
+                }
+                unsigned pre = __popc(cm);
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned v = __shfl_up_sync(0xffffffffu, pre, off);
+                    if (lane >= off) pre += v;
+                }
+                const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+                for (unsigned t0 = 0; t0 < total; t0 += 32) {
+                    const unsigned P = t0 + (unsigned)lane;
+                    int bc = 0;  // the pair's centroid: columns whose prefix is <= P
+#pragma unroll
+                    for (int step = 16; step; step >>= 1)
+                        if (__shfl_sync(0xffffffffu, pre, bc + step - 1) <= P) bc += step;
+                    const unsigned cmb = __shfl_sync(0xffffffffu, cm, bc);
+                    const unsigned below = __shfl_sync(0xffffffffu, pre, bc > 0 ? bc - 1 : 0);
+                    const unsigned kk = P - (bc > 0 ? below : 0u);
+                    int fl = 0;  // its fiber: the (kk+1)-th set bit of the column's mask
+#pragma unroll
+                    for (int step = 16; step; step >>= 1)
+                        if ((unsigned)__popc(cmb & (unsigned)((1ull << (fl + step)) - 1ull)) <= kk)
+                            fl += step;
+                    const int j = 32 * cc + bc;
+                    unsigned live = 0u;
+                    float md = 0.0f, mr = 0.0f;
+                    if (P < total) {
+                        const float4* r = g.end_sp + 3 * (size_t)j;
+                        const float4 q10 = __ldg(r + 1);  // w: theta^2
+                        const float bound = pair_bound2(
+                            at, q10.w, key_bound2(fz_best(S, fl), at.cls));
+                        live = fz_phase_a(S.f + fl * FZ_STRIDE, __ldg(r), q10, __ldg(r + 2),
+                                          bound, at.cls, md, mr, npd);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, live != 0u);
+                    if (live) {
+                        const int e = qn + __popc(bal & ((1u << lane) - 1u));
+                        S.qm[e] = make_float2(md, mr);
+                        S.qe[e] = (unsigned)fl | (live << 5) | ((unsigned)j << 7);
+                    }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {  // one coherent round of test3/test4: the newest 32
+                        qn -= 32;
+                        fz_phase_b<EXT>(S, qn + lane, at, g, perm, f0, npd);
+                        __syncwarp();
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (qn > 0) {  // the group's last queued pairs
+            if (lane < qn) fz_phase_b<EXT>(S, lane, at, g, perm, f0, npd);
+            qn = 0;
+        }
+        __syncwarp();
+        // 4. results in the caller's order
+        if (lane < rows_in) {
+            const unsigned long long k = S.key[lane];
+            long long o2 = my_src;
+            int* lab = labels;
+            float* dst = dist;
+            int* ci = cidx;
+            unsigned char* ori = orient;
+            if (src.table) {
+                const BatchEntry& e = src.table[src.subject(o2)];
+                lab = e.labels;
+                dst = e.dist;
+                ci = nullptr;
+                ori = nullptr;
+                o2 -= e.first;
+            }
+            if (k == NAN_KEY || k == ~0ull) {
+                lab[o2] = -1;
+                if (dst) dst[o2] = k == NAN_KEY ? NAN : INFINITY;
+                if (ci) ci[o2] = -1;
+                if (ori) ori[o2] = 0;
+            } else {
+                const int sidx = (int)((k & 0xffffffffull) >> 1);
+                const float kf = __uint_as_float((unsigned)(k >> 32));
+                lab[o2] = at.bundle[sidx];
+                if (dst) dst[o2] = at.cls != CLS_EQ2 ? kf : sqrtf(kf);
+                if (ci) ci[o2] = at.perm[sidx];
+                if (ori) ori[o2] = (unsigned char)(k & 1ull);
+            }
+        }
+    }
+    unsigned long long tot = npd;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        tot += __shfl_down_sync(0xffffffffu, tot, off);
+        screened += __shfl_down_sync(0xffffffffu, screened, off);
+        surv += __shfl_down_sync(0xffffffffu, surv, off);
+    }
+    if (lane == 0) {
+        if (surv) atomicAdd(g.cnt + 2, surv);
+        if (screened) atomicAdd(g.cnt + 3, screened);
+        if (tot) atomicAdd(g.cnt + 5, tot);
+    }
+}
+
+__global__ void k_gemm_stats(const unsigned long long* __restrict__ cnt, long long pairs,
+                             long long* __restrict__ stats) {
+    stats[0] = pairs;
+    stats[1] = (long long)cnt[2];
+    stats[2] = (long long)cnt[1];
+    stats[3] = (long long)cnt[3];
+    stats[4] = (long long)cnt[5];
+}
+
 constexpr unsigned DONE_ENTRY = 0xFFFFFFFFu;  // queue entry already tested
 
 // test3 and test4 of one queued pair (its live orientations and partial maxima from phase A),
@@ -1517,14 +1820,15 @@ seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, int max_per_
         (e = cudaMalloc(&g->cen_sp, (size_t)at.M * CROW4 * sizeof(float4))) ||
         (e = cudaMalloc(&g->thr2_sp, (size_t)at.M * sizeof(float))) ||
         (e = cudaMalloc(&g->ctr_sp, (size_t)at.M * sizeof(float4))) ||
-        (e = cudaMalloc(&g->scr_sp, (size_t)at.M * sizeof(float4))))
+        (e = cudaMalloc(&g->scr_sp, (size_t)(at.M + 31) / 32 * 32 * sizeof(float4))) ||
+        (e = cudaMalloc(&g->end_sp, (size_t)at.M * 3 * sizeof(float4))))
         return cuda_fail(e, "gemm spatial order");
     // the host array lives until the caller synchronizes the stream
     if ((e = cudaMemcpyAsync(g->sp_s, sp_host, (size_t)at.M * sizeof(int), cudaMemcpyHostToDevice,
                              st)))
         return cuda_fail(e, "gemm spatial order");
-    k_prep_spatial<<<(at.M + 7) / 8, dim3(32, 8), 0, st>>>(at, g->sp_s, g->cen_sp, g->thr2_sp,
-                                                          g->ctr_sp, g->scr_sp);
+    k_prep_spatial<<<((at.M + 31) / 32 * 32 + 7) / 8, dim3(32, 8), 0, st>>>(at, g->sp_s, g->cen_sp, g->thr2_sp,
+                                                          g->ctr_sp, g->scr_sp, g->end_sp);
     g->cols = 2 * at.M;
     g->cols_pad = (g->cols + COL_ALIGN - 1) / COL_ALIGN * COL_ALIGN;
     if ((e = cudaMalloc(&g->b_bf16, (size_t)g->cols_pad * 64 * 2)) ||
@@ -1556,13 +1860,14 @@ void free_gemm_atlas(GemmAtlas* g) {
     cudaFree(g->thr2_sp);
     cudaFree(g->ctr_sp);
     cudaFree(g->scr_sp);
+    cudaFree(g->end_sp);
     cudaFree(g->stats);
     *g = GemmAtlas{};
 }
 
 // One GEMM-mode call over n fibers: sizes, the scratch layout and the tensor maps.
 struct GemmCall {
-    bool culled, tf32, inv;
+    bool culled, fused, tf32, inv;
     GemmShape sh;
     long long n, n_pad, n_units;
     int cols, n_tiles, n_chunks, awords, sms;
@@ -1577,7 +1882,8 @@ struct GemmCall {
 // scratch on `st` once the call's work is enqueued) and encodes the tensor maps.
 seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch, long long n,
                       int mode, int config, cudaStream_t st, GemmCall* c) {
-    c->culled = mode == SEG_MODE_PLAIN_CULLED;  // test1 on CUDA cores, no operand
+    c->fused = mode == SEG_MODE_CULLED_FUSED;  // one kernel after the sort, no record list
+    c->culled = c->fused || mode == SEG_MODE_PLAIN_CULLED;  // test1 on CUDA cores, no operand
     c->tf32 = mode == SEG_MODE_GEMM_TF32 || mode == SEG_MODE_GEMM_INV_TF32;
     c->inv = c->culled || mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32;
     const bool culled = c->culled, tf32 = c->tf32, inv = c->inv;
@@ -1612,17 +1918,22 @@ seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
                : (long long)sms * EPI_WARPS;
     long long cap = n_pad / 32 * ga->rec_per_group + 65536 + writers * SLOT_GRAB;
     if (ga->cap_limit > 0 && ga->cap_limit < cap) cap = ga->cap_limit;
+    if (c->fused) cap = 0;  // keys, flags and the sorted rows are not used either
+    if (c->fused && at.M >= FZ_MAX_M)
+        return fail(SEG_ERR_UNSUPPORTED, "seg_label: %d centroids exceed the fused mode's %d",
+                    at.M, FZ_MAX_M);
     const size_t elem = culled ? 0 : tf32 ? 4 : 2;
     const size_t off_alpha = align256((size_t)n_pad * sh.ke * elem);
+    // (the fused mode uses the count words, the order, the bins and the chunk boxes only)
     const size_t off_key = off_alpha + align256((size_t)n_pad * 4);
-    const size_t off_flag = off_key + align256((size_t)n * 8);
-    const size_t off_cnt = off_flag + align256((size_t)n);
+    const size_t off_flag = off_key + align256(c->fused ? 0 : (size_t)n * 8);
+    const size_t off_cnt = off_flag + align256(c->fused ? 0 : (size_t)n);
     const size_t off_perm = off_cnt + 256;
     const size_t off_bin = off_perm + align256((size_t)n * 4);
     const size_t off_hist = off_bin + align256((size_t)n * 4);
     const size_t off_top = off_hist + (size_t)NBINS * 4;
     const size_t off_fs = off_top + (size_t)NTOP * 4;
-    const size_t off_ubox = off_fs + (size_t)n_pad * CROW * 4;
+    const size_t off_ubox = off_fs + (c->fused ? 0 : (size_t)n_pad * CROW * 4);
     const size_t off_tbox = off_ubox + align256((size_t)(n_pad / 32) * 32);
     const size_t off_amask = off_tbox + align256((size_t)n_chunks * 32);
     const size_t off_hdr = off_amask + align256((size_t)n_units * awords * 8);
@@ -1654,6 +1965,7 @@ seg_status gemm_setup(const AtlasView& at, GemmAtlas* ga, ScratchArena* scratch,
     g.amask = c->amask;
     g.awords = awords;
     g.cen_sp = ga->cen_sp;
+    g.end_sp = ga->end_sp;
     g.thr2_sp = ga->thr2_sp;
     g.sp_s = ga->sp_s;
     g.cap = cap;
@@ -1683,7 +1995,7 @@ cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, 
     const long long n = c.n;
     const int sms = c.sms;
     cudaError_t e = cudaMemsetAsync(g.cnt, 0, 256, st);
-    if (!e) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
+    if (!e && !c.fused) e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_SORT, st);
         const unsigned nb = (unsigned)((n + 255) / 256);
@@ -1693,6 +2005,21 @@ cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, 
         if (!e) k_bin_scan_top<<<1, 32, 0, st>>>(c.top);
         if (!e) k_bin_scatter<<<nb, 256, 0, st>>>(c.bin, n, c.hist, c.top, c.perm);
         if (!e) e = cudaGetLastError();
+    }
+    if (!e && c.fused) {
+        ProfScope ps(prof, PROF_FUSED, st);
+        k_tile_box<<<(c.n_chunks + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M, 32, c.n_chunks,
+                                                            c.tbox);
+        const long long n_groups = (n + 31) / 32;
+        const bool ext = at.cls != CLS_EQ2 || at.multi != nullptr;
+        auto kern = ext ? k_fused<true> : k_fused<false>;
+        kern<<<(unsigned)std::min<long long>((n_groups + FZ_WARPS - 1) / FZ_WARPS,
+                                             (long long)sms * FZ_CTAS),
+               FZ_WARPS * 32, FZ_WARPS * sizeof(FzWarp), st>>>(
+            src, c.perm, n, n_groups, at, g, ga->scr_sp, c.tbox, c.n_chunks, labels, dist, cidx,
+            orient);
+        if (!dbg_bits) k_gemm_stats<<<1, 1, 0, st>>>(g.cnt, n * (long long)c.cols, ga->stats);
+        return cudaGetLastError();
     }
     if (!e) {
         ProfScope ps(prof, PROF_GEMM_PREP, st);

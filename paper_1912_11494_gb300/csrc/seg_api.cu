@@ -161,7 +161,7 @@ struct seg_atlas {
     cudaEvent_t hev[SEG_HOST_CHUNKS + 2] = {};
     std::mutex host_mu;
     BatchState batch{};
-    int config[6] = {0, 0, 0, 0, 0, 0};  // tile-shape selection per seg_mode
+    int config[7] = {0, 0, 0, 0, 0, 0, 0};  // tile-shape selection per seg_mode
     Profiler prof;
     std::mutex mu;  // guards scratch growth and the batch graph cache
 };
@@ -359,7 +359,7 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
         return fail(SEG_ERR_INVALID_ARG, "seg_label: NULL fibers or labels");
     if (unaligned4(d_fibers) || unaligned4(d_labels) || unaligned4(d_dist) || unaligned4(d_cidx))
         return fail(SEG_ERR_INVALID_ARG, "seg_label: a buffer is not 4-byte aligned");
-    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_label: unknown mode %d", (int)mode);
     if (n == 0) return SEG_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -381,7 +381,7 @@ seg_status seg_label_multi(const seg_atlas* atlas, const float* d_fibers, int64_
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: n=%lld < 0", (long long)n);
-    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_multi: unknown mode %d", (int)mode);
     const int64_t need = ((int64_t)atlas->view.B + 31) / 32;
     if (words_per_fiber < need)
@@ -418,7 +418,7 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_host: n=%lld < 0", (long long)n);
     if (n > 0 && (!h_fibers || !h_labels))
         return fail(SEG_ERR_INVALID_ARG, "seg_label_host: NULL fibers or labels");
-    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_host: unknown mode %d", (int)mode);
     if (n == 0) return SEG_OK;
     seg_atlas* a = const_cast<seg_atlas*>(atlas);
@@ -499,7 +499,7 @@ seg_status seg_label_streamlines(const seg_atlas* atlas, const float* d_points,
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: n < 0");
-    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_streamlines: unknown mode %d", (int)mode);
     if (n == 0) return SEG_OK;
     if (!d_offsets || !d_labels)
@@ -531,7 +531,7 @@ seg_status seg_label_batch(const seg_atlas* atlas, int32_t nsubj, const float* c
     if (nsubj == 0) return SEG_OK;
     if (!h_fibers || !h_counts || !h_labels)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: NULL pointer array");
-    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_label_batch: unknown mode %d", (int)mode);
     for (int s = 0; s < nsubj; ++s) {
         if (h_counts[s] < 0)
@@ -591,7 +591,8 @@ int32_t seg_num_configs(seg_mode mode) {
         case SEG_MODE_GEMM_TF32:
         case SEG_MODE_GEMM_INV_BF16:
         case SEG_MODE_GEMM_INV_TF32: return gemm_num_configs();
-        case SEG_MODE_PLAIN_CULLED: return 1;
+        case SEG_MODE_PLAIN_CULLED:
+        case SEG_MODE_CULLED_FUSED: return 1;
     }
     return 0;
 }
@@ -666,7 +667,7 @@ seg_status seg_refine_affine(const seg_atlas* atlas, const float* d_fibers, int6
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: atlas is NULL");
     if (n <= 0 || !d_fibers || !h_affine12)
         return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: no fibers or NULL affine");
-    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_PLAIN || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: unknown mode %d", (int)mode);
     if (iters < 0 || !(step_mm > 0.0) || !std::isfinite(step_mm))
         return fail(SEG_ERR_INVALID_ARG, "seg_refine_affine: iters=%d step=%g", iters, step_mm);
@@ -711,8 +712,11 @@ seg_status seg_gemm_screen_bits(const seg_atlas* atlas, const float* d_fibers, i
     g_last_error.clear();
     if (!atlas) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: atlas is NULL");
     if (n < 0) return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: n < 0");
-    if ((int)mode < SEG_MODE_GEMM_BF16 || (int)mode > SEG_MODE_PLAIN_CULLED)
+    if ((int)mode < SEG_MODE_GEMM_BF16 || (int)mode > SEG_MODE_CULLED_FUSED)
         return fail(SEG_ERR_INVALID_ARG, "seg_gemm_screen_bits: mode %d has no screen",
+                    (int)mode);
+    if (mode == SEG_MODE_CULLED_FUSED)
+        return fail(SEG_ERR_UNSUPPORTED, "seg_gemm_screen_bits: mode %d has no separate screen",
                     (int)mode);
     const bool inv = mode == SEG_MODE_GEMM_INV_BF16 || mode == SEG_MODE_GEMM_INV_TF32 ||
                      mode == SEG_MODE_PLAIN_CULLED;
@@ -751,7 +755,8 @@ seg_status seg_profile_read(seg_atlas* atlas, const char* kernel, int64_t* launc
     if (!atlas || !kernel) return fail(SEG_ERR_INVALID_ARG, "seg_profile_read: NULL argument");
     static const char* names[PROF_SLOTS] = {"plain",         "batch", "gemm_prep",
                                             "gemm_screen",   "gemm_exact", "gemm_finalize",
-                                            "grad",          "gemm_sort", "cull_screen"};
+                                            "grad",          "gemm_sort", "cull_screen",
+                                            "culled_fused"};
     int slot = -1;
     for (int k = 0; k < PROF_SLOTS; ++k)
         if (strcmp(kernel, names[k]) == 0) slot = k;

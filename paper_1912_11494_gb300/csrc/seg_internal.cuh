@@ -17,7 +17,8 @@ seg_status cuda_fail(cudaError_t e, const char* what);
 
 // Event-pair timing of the library's kernels (seg_profile_enable / seg_profile_read).
 enum ProfSlot { PROF_PLAIN = 0, PROF_BATCH, PROF_GEMM_PREP, PROF_GEMM_SCREEN, PROF_GEMM_EXACT,
-                PROF_GEMM_FINAL, PROF_GRAD, PROF_GEMM_SORT, PROF_CULL_SCREEN, PROF_SLOTS };
+                PROF_GEMM_FINAL, PROF_GRAD, PROF_GEMM_SORT, PROF_CULL_SCREEN, PROF_FUSED,
+                PROF_SLOTS };
 struct Profiler {
     bool enabled = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;  // reusable events
@@ -71,7 +72,10 @@ struct GemmAtlas {
     float4* cen_sp = nullptr; // [M][21] centroid rows in spatial order, point-major
     float* thr2_sp = nullptr; // [M] theta^2 in spatial order
     float4* ctr_sp = nullptr; // [M] centre point and theta^2 in spatial order
-    float4* scr_sp = nullptr; // [M] the test1 screen row (AtlasView::scr2) in spatial order
+    float4* scr_sp = nullptr; // [M rounded up to 32] the test1 screen row (AtlasView::scr2) in
+                              // spatial order; the pad (0, 0, 0, -inf) passes no fiber
+    float4* end_sp = nullptr; // [M][3] points 0, 10, 20 in spatial order (w: the length,
+                              // theta^2, 0): what test1 and test2 read, 48 bytes a centroid
     long long* stats = nullptr;  // [5] pairs, survivors, overflow fibers, screened pairs,
                                  // point distances of the exact re-check
     long long cap_limit = 0;     // caller's limit on survivor block records (0: none)

@@ -47,7 +47,7 @@ def batch(at, fibs, mode, with_dist=True):
 
 
 @pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16",
-                                  "plain_culled"])
+                                  "plain_culled", "culled_fused"])
 def test_batch_equals_single_calls(env, mode):
     dev, a, at = env
     fibs = subjects(a, [0, 1, 33, 1000, 5000, 257, 31], 100, dev)
@@ -91,7 +91,8 @@ def test_every_tile_shape_in_batch(env):
     binding.seg_set_config(at, "plain", 0)
 
 
-@pytest.mark.parametrize("mode", ["gemm_bf16", "plain_culled", "gemm_inv_tf32"])
+@pytest.mark.parametrize("mode", ["gemm_bf16", "plain_culled", "gemm_inv_tf32",
+                                  "culled_fused"])
 def test_graph_replay_recapture_and_back_to_back(env, mode):
     """GEMM and culled modes: replays with the same shape, recaptures when the total or the
     subject count changes, and back-to-back calls with no synchronisation in between (the two
@@ -127,7 +128,7 @@ def c4(env):
     return atlas, at, fibs
 
 
-@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "plain_culled"])
+@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "plain_culled", "culled_fused"])
 def test_full_size_batch(env, c4, mode):
     """The full 16-subject batch in one call: every fiber of every subject equal to a single
     seg_label call on that subject (whose full-size parity is checked fiber by fiber in

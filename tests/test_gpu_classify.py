@@ -17,7 +17,8 @@ from paper_1912_11494_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled"]
+MODES = ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled",
+         "culled_fused"]
 DIST_TOL = 1e-3
 
 
@@ -145,7 +146,7 @@ def test_classification_full_size(dev, full_size, cls):
     eq2 = run(at, fib, dev, "plain")
     binding.seg_set_classification(at, cls)
     ref = run(at, fib, dev, "plain")
-    for mode in ("gemm_bf16", "plain_culled"):
+    for mode in ("gemm_bf16", "plain_culled", "culled_fused"):
         got = run(at, fib, dev, mode)
         for x, y in zip(ref, got):
             np.testing.assert_array_equal(x, y)

@@ -9,7 +9,8 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled"]
+MODES = ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled",
+         "culled_fused"]
 
 
 @pytest.fixture(scope="module")
@@ -153,7 +154,7 @@ def test_full_size_parity_every_fiber(dev, mode, full_size, full_size_ref):
 
 
 @pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32",
-                                  "plain_culled"])
+                                  "plain_culled", "culled_fused"])
 def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
     """The prune is conservative and survivors go through the same FP32 exact test, so the GEMM
     modes reproduce the plain kernel bit for bit on every fiber, not only the decidable ones."""
@@ -164,10 +165,10 @@ def test_gemm_equals_plain_everywhere(dev, mode, small_workload, full_size):
         for x, y in zip(ref, got):
             np.testing.assert_array_equal(x, y)
         st = binding.seg_gemm_stats(at)
-        cols = atlas_np.M if ("inv" in mode or mode == "plain_culled") else 2 * atlas_np.M
+        cols = atlas_np.M if ("inv" in mode or "culled" in mode) else 2 * atlas_np.M
         assert st["pairs"] == len(fib) * cols
         # own bundle alone is 2% at M=1,000; test1 alone keeps more than the GEMM bounds
-        assert 0 < st["survivors"] < (0.2 if mode == "plain_culled" else 0.05) * st["pairs"]
+        assert 0 < st["survivors"] < (0.2 if "culled" in mode else 0.05) * st["pairs"]
         assert st["overflow_fibers"] == 0
         # every listed pair runs test1 at least; the culled blocks are never computed
         assert st["point_distances"] >= st["survivors"]
@@ -185,7 +186,8 @@ def test_no_survivor_overflow_at_any_size(dev, full_size, n):
         assert binding.seg_gemm_stats(at)["overflow_fibers"] == 0, mode
 
 
-@pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled"])
+@pytest.mark.parametrize("mode", ["gemm_bf16", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled",
+                                  "culled_fused"])
 def test_gemm_locality_order_extremes(dev, mode):
     """The GEMM modes visit fibers in the order of their centre point's 2 mm cell. Centres far
     outside the cell grid (clamped to its border), thousands of fibers in one cell, and a NaN
@@ -312,7 +314,7 @@ def test_gemm_column_limit(dev):
     with pytest.raises(binding.SegError):
         run(at, fib, dev, "gemm_bf16")
     ref = run(at, fib, dev, "plain")
-    for mode in ("gemm_inv_bf16", "plain_culled"):
+    for mode in ("gemm_inv_bf16", "plain_culled", "culled_fused"):
         got = run(at, fib, dev, mode)
         for x, y in zip(ref, got):
             np.testing.assert_array_equal(x, y)

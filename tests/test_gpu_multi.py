@@ -11,7 +11,8 @@ from paper_1912_11494_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled"]
+MODES = ["plain", "gemm_bf16", "gemm_tf32", "gemm_inv_bf16", "gemm_inv_tf32", "plain_culled",
+         "culled_fused"]
 
 
 @pytest.fixture(scope="module")
@@ -97,7 +98,7 @@ def test_multi_label_full_size(dev):
     a, fib = synth.workload("subject4145k_atlas10k", device="cuda")
     at = make_atlas(a, dev)
     ref = multi(at, fib, dev, "plain")
-    for mode in ("gemm_bf16", "plain_culled"):
+    for mode in ("gemm_bf16", "plain_culled", "culled_fused"):
         got = multi(at, fib, dev, mode)
         for x, y in zip(ref, got):
             np.testing.assert_array_equal(x, y)

@@ -86,7 +86,7 @@ def test_resample_edge_cases(dev):
     assert got[0, 20, 0] == 20.0 and got[0, 0, 0] == 0.0
 
 
-@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "plain_culled"])
+@pytest.mark.parametrize("mode", ["plain", "gemm_bf16", "plain_culled", "culled_fused"])
 def test_label_streamlines(dev, mode):
     """seg_label_streamlines equals seg_resample followed by seg_label, and its labels match the
     oracle's labelling of the same resampled fibers."""

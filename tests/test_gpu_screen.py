@@ -98,6 +98,8 @@ def test_screen_bits_rejects_bad_arguments(case):
     f = torch.as_tensor(fib[:10], device=dev)
     with pytest.raises(binding.SegError):
         binding.seg_gemm_screen_bits(at, f, "plain")
+    with pytest.raises(binding.SegError):  # one kernel: no separate screen to read
+        binding.seg_gemm_screen_bits(at, f, "culled_fused")
     bits = torch.empty((10, 1), dtype=torch.int32, device=dev)
     rc = binding.lib().seg_gemm_screen_bits(at.handle, f.data_ptr(), 10, 1, bits.data_ptr(), 1,
                                             None)
