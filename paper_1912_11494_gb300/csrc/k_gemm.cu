@@ -445,13 +445,18 @@ __device__ inline UnitBox unit_box(const float4* __restrict__ ubox, long long u,
     return b;
 }
 
-__device__ inline bool block_active(const UnitBox& b, const float4* __restrict__ tbox, int t) {
+// Squared gap between a unit's centre-point box and tile t's (0 where they meet).
+__device__ inline float block_gap2(const UnitBox& b, const float4* __restrict__ tbox, int t) {
     const float4 lo = __ldg(tbox + 2 * t), hi = __ldg(tbox + 2 * t + 1);
     const float gx = fmaxf(0.0f, fmaxf(lo.x - b.hx, b.lx - hi.x));
     const float gy = fmaxf(0.0f, fmaxf(lo.y - b.hy, b.ly - hi.y));
     const float gz = fmaxf(0.0f, fmaxf(lo.z - b.hz, b.lz - hi.z));
-    const float lb2 = gx * gx + gy * gy + gz * gz;
-    return !(lb2 > lo.w * 1.0001f + 1e-3f);  // lo.w: max theta^2 of the tile
+    return gx * gx + gy * gy + gz * gz;
+}
+
+__device__ inline bool block_active(const UnitBox& b, const float4* __restrict__ tbox, int t) {
+    const float lb2 = block_gap2(b, tbox, t);
+    return !(lb2 > __ldg(&tbox[2 * t].w) * 1.0001f + 1e-3f);  // lo.w: max theta^2 of the tile
 }
 
 constexpr int MAXW = 64;  // mask words per unit: at most 4096 chunks (131,072 columns)
@@ -524,12 +529,13 @@ __global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, in
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     float4 lo = make_float4(INFINITY, INFINITY, INFINITY, -INFINITY);
-    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, INFINITY);
     for (int c = t * per; c < min(M, (t + 1) * per); ++c) {
         const float4 v = ctr_sp[c];
         lo.x = fminf(lo.x, v.x), lo.y = fminf(lo.y, v.y), lo.z = fminf(lo.z, v.z);
         hi.x = fmaxf(hi.x, v.x), hi.y = fmaxf(hi.y, v.y), hi.z = fmaxf(hi.z, v.z);
-        lo.w = fmaxf(lo.w, v.w);
+        lo.w = fmaxf(lo.w, v.w);  // the tile's largest theta^2
+        hi.w = fminf(hi.w, v.w);  // and its smallest
     }
     tbox[2 * t] = lo;
     tbox[2 * t + 1] = hi;
@@ -1254,13 +1260,25 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                 const int cc = k0 + __ffs(act) - 1;
                 act &= act - 1;
                 S.q[lane] = __ldg(scr_sp + 32 * (size_t)cc + lane);  // padded to whole chunks
+                // test1 against min(theta^2, the fiber's best so far): the dot-product form's
+                // threshold h rises by half of (theta^2 - best) where that is positive; with the
+                // chunk's smallest theta^2 in place of each centroid's and a margin far above
+                // the rounding of the difference and of the sum, the rise never drops a pair
+                // the exact test could accept (its bound is the same minimum)
+                float he = h;
+                if (!at.multi) {
+                    const float tmin = __ldg(&tbox[2 * cc + 1].w);
+                    const float bb = key_bound2(fz_best(S, lane), at.cls);
+                    he = h + fmaxf(0.0f, fmaf(0.5f, tmin - bb,
+                                              -(1e-5f * (tmin + fabsf(h)) + 1e-4f)));
+                }
                 __syncwarp();
                 unsigned m = 0u;  // test1 (dot-product form with its slack) of this lane's fiber
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const float4 q = S.q[i];  // the same row for every lane: a broadcast
                     const float t = fmaf(z, q.z, fmaf(y, q.y, fmaf(x, q.x, q.w)));
-                    m |= (t >= h ? 1u : 0u) << i;
+                    m |= (t >= he ? 1u : 0u) << i;
                 }
                 screened += 32;
                 __syncwarp();
