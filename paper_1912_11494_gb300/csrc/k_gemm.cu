@@ -1130,22 +1130,22 @@ __device__ __forceinline__ float fz_best(const FzWarp& S, int fl) {
 // against the centroid's points 0, 10, 20, both orientations (the one the end points infer with
 // cls == CLS_PAPER). The same arithmetic as the exact kernel's. Returns the live orientations (bit 0 direct, bit 1
 // reversed) and their partial maxima.
-__device__ __forceinline__ float pd2q(const float* a, int i, float4 q) {
-    const float dx = a[3 * i] - q.x;
-    const float dy = a[3 * i + 1] - q.y;
-    const float dz = a[3 * i + 2] - q.z;
+__device__ __forceinline__ float pd2q(float3 p, float4 q) {
+    const float dx = p.x - q.x;
+    const float dy = p.y - q.y;
+    const float dz = p.z - q.z;
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
-__device__ __forceinline__ unsigned fz_phase_a(const float* a, float4 q0, float4 q10, float4 q20,
-                                               float bound, int cls, float& md, float& mr,
-                                               unsigned& npd) {
-    constexpr int L = NPTS - 1;
-    const float c = pd2q(a, CENTRE, q10);
+// p0, p10, p20: the fiber's points 0, 10, 20; q0, q10, q20: the centroid's.
+__device__ __forceinline__ unsigned fz_phase_a(float3 p0, float3 p10, float3 p20, float4 q0,
+                                               float4 q10, float4 q20, float bound, int cls,
+                                               float& md, float& mr, unsigned& npd) {
+    const float c = pd2q(p10, q10);
     npd += 1;
     if (!(c <= bound)) return 0u;
-    md = fmaxf(c, fmaxf(pd2q(a, 0, q0), pd2q(a, L, q20)));
-    mr = fmaxf(c, fmaxf(pd2q(a, 0, q20), pd2q(a, L, q0)));
+    md = fmaxf(c, fmaxf(pd2q(p0, q0), pd2q(p20, q20)));
+    mr = fmaxf(c, fmaxf(pd2q(p0, q20), pd2q(p20, q0)));
     npd += 4;
     bool ad = md <= bound, ar = mr <= bound;
     if (cls == CLS_PAPER) {  // direction inferred from the end points
@@ -1297,31 +1297,48 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                     if (lane >= off) pre += v;
                 }
                 const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
-                for (unsigned t0 = 0; t0 < total; t0 += 32) {
-                    const unsigned P = t0 + (unsigned)lane;
-                    int bc = 0;  // the pair's centroid: columns whose prefix is <= P
+                // a round's pair P (column-major): its centroid column bc (the columns whose
+                // prefix is <= P) and fiber fl (the (k+1)-th set bit of that column's mask);
+                // the next round's is located while this round's loads are in flight
+                auto locate = [&](unsigned Pq, int& bc_o, int& fl_o) {
+                    int bc = 0;
 #pragma unroll
                     for (int step = 16; step; step >>= 1)
-                        if (__shfl_sync(0xffffffffu, pre, bc + step - 1) <= P) bc += step;
+                        if (__shfl_sync(0xffffffffu, pre, bc + step - 1) <= Pq) bc += step;
                     const unsigned cmb = __shfl_sync(0xffffffffu, cm, bc);
                     const unsigned below = __shfl_sync(0xffffffffu, pre, bc > 0 ? bc - 1 : 0);
-                    const unsigned kk = P - (bc > 0 ? below : 0u);
-                    int fl = 0;  // its fiber: the (kk+1)-th set bit of the column's mask
+                    const unsigned kk = Pq - (bc > 0 ? below : 0u);
+                    int fl = 0;
 #pragma unroll
-                    for (int step = 16; step; step >>= 1)
-                        if ((unsigned)__popc(cmb & (unsigned)((1ull << (fl + step)) - 1ull)) <= kk)
-                            fl += step;
-                    const int j = 32 * cc + bc;
+                    for (int step = 16; step; step >>= 1)  // fl + step <= 31
+                        if ((unsigned)__popc(cmb & ((1u << (fl + step)) - 1u)) <= kk) fl += step;
+                    bc_o = bc;
+                    fl_o = fl;
+                };
+                int bc, fl;
+                locate((unsigned)lane, bc, fl);
+                for (unsigned t0 = 0; t0 < total; t0 += 32) {
+                    const unsigned P = t0 + (unsigned)lane;
+                    // loads for every lane (a lane past the total reads a valid row unused)
+                    const int j = min(32 * cc + bc, at.M - 1);
+                    const float4* r = g.end_sp + 3 * (size_t)j;
+                    const float4 q10 = __ldg(r + 1);  // w: theta^2
+                    const float4 q0 = __ldg(r), q20 = __ldg(r + 2);
+                    const float* a = S.f + fl * FZ_STRIDE;
+                    const float3 p0 = make_float3(a[0], a[1], a[2]);
+                    const float3 p10 = make_float3(a[3 * CENTRE], a[3 * CENTRE + 1],
+                                                   a[3 * CENTRE + 2]);
+                    const float3 p20 = make_float3(a[3 * (NPTS - 1)], a[3 * (NPTS - 1) + 1],
+                                                   a[3 * (NPTS - 1) + 2]);
+                    const float bestv = fz_best(S, fl);
+                    int nbc = 0, nfl = 0;
+                    if (t0 + 32 < total) locate(P + 32, nbc, nfl);
                     unsigned live = 0u;
                     float md = 0.0f, mr = 0.0f;
-                    if (P < total) {
-                        const float4* r = g.end_sp + 3 * (size_t)j;
-                        const float4 q10 = __ldg(r + 1);  // w: theta^2
-                        const float bound = pair_bound2(
-                            at, q10.w, key_bound2(fz_best(S, fl), at.cls));
-                        live = fz_phase_a(S.f + fl * FZ_STRIDE, __ldg(r), q10, __ldg(r + 2),
-                                          bound, at.cls, md, mr, npd);
-                    }
+                    if (P < total)
+                        live = fz_phase_a(p0, p10, p20, q0, q10, q20,
+                                          pair_bound2(at, q10.w, key_bound2(bestv, at.cls)),
+                                          at.cls, md, mr, npd);
                     const unsigned bal = __ballot_sync(0xffffffffu, live != 0u);
                     if (live) {
                         const int e = qn + __popc(bal & ((1u << lane) - 1u));
@@ -1335,6 +1352,8 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                         fz_phase_b<EXT>(S, qn + lane, at, g, perm, f0, npd);
                         __syncwarp();
                     }
+                    bc = nbc;
+                    fl = nfl;
                 }
                 __syncwarp();
             }
