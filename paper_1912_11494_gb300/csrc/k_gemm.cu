@@ -100,8 +100,9 @@ struct GemmScratch {
     unsigned* mask;               // [cap][32] surviving columns of each of the 32 fibers
     unsigned long long wait_ns;   // limit of the screen's bounded waits (AtlasView::wait_ns)
     unsigned long long* cnt;      // [0] records reserved, [1] fibers flagged, [2] survivors,
-                                  // [3] pairs in the blocks the tensor cores computed, [4] run
-                                  // counter of the exact kernel, [5] its point distances
+                                  // [3] pairs in the blocks the tensor cores computed, [4] work
+                                  // counter (the exact kernel's runs, the fused kernel's groups),
+                                  // [5] point distances of the exact test
     long long cap;
 };
 
@@ -1204,8 +1205,12 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
     FzWarp& S = reinterpret_cast<FzWarp*>(fz_smem)[w];
     unsigned long long screened = 0, surv = 0;
     unsigned npd = 0;
-    const long long W = (long long)gridDim.x * FZ_WARPS;
-    for (long long grp = (long long)blockIdx.x * FZ_WARPS + w; grp < n_groups; grp += W) {
+    // groups taken from a counter (their costs vary with the density of the atlas around
+    // them; a fixed stride left a long tail), the next one fetched while this one finishes
+    long long grp = 0;
+    if (lane == 0) grp = (long long)atomicAdd(g.cnt + 4, 1ull);
+    grp = __shfl_sync(0xffffffffu, grp, 0);
+    while (grp < n_groups) {
         const long long f0 = grp * 32;
         const int rows_in = (int)max(0LL, min(32LL, n - f0));
         int qn = 0;  // queued pairs (warp-uniform)
@@ -1363,6 +1368,8 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
             qn = 0;
         }
         __syncwarp();
+        long long next = 0;
+        if (lane == 0) next = (long long)atomicAdd(g.cnt + 4, 1ull);
         // 4. results in the caller's order
         if (lane < rows_in) {
             const unsigned long long k = S.key[lane];
@@ -1393,6 +1400,7 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                 if (ori) ori[o2] = (unsigned char)(k & 1ull);
             }
         }
+        grp = __shfl_sync(0xffffffffu, next, 0);
     }
     unsigned long long tot = npd;
 #pragma unroll
@@ -2050,6 +2058,10 @@ cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, 
         const long long n_groups = (n + 31) / 32;
         const bool ext = at.cls != CLS_EQ2 || at.multi != nullptr;
         auto kern = ext ? k_fused<true> : k_fused<false>;
+        const int smem = FZ_WARPS * (int)sizeof(FzWarp);
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e) return e;
         kern<<<(unsigned)std::min<long long>((n_groups + FZ_WARPS - 1) / FZ_WARPS,
                                              (long long)sms * FZ_CTAS),
                FZ_WARPS * 32, FZ_WARPS * sizeof(FzWarp), st>>>(
