@@ -1097,22 +1097,25 @@ __device__ __forceinline__ float rest17(const float* a, const float4* b, float m
 // One warp owns a 32-fiber group of the locality order from start to finish: it gathers the
 // group's 32 rows from the caller's array into shared memory once (odd row stride, so lanes
 // reading different rows at one column never share a bank), tests the group's centre-point box
-// against the 32-centroid chunks (a ballot over 32 chunks at a time), runs test1 in dot-product
-// form for every pair of a chunk in reach (the chunk's 32 screen rows read as broadcasts), and
-// runs the exact test (Section 2.3: test1..test4, both orientations, early exits) on that
-// chunk's survivors at once: 32 pairs per round in column-major order (the rows' masks
-// transposed by ballots), so the lanes of a round mostly read the same centroid row (L1
-// broadcasts) while each reads its own fiber's points from shared memory. Each fiber's packed
-// key and best value live in shared memory (atomicMin), so there is no sorted copy, no record
-// list and no overflow path; the bound tightens as the chunks are visited in spatial order.
+// against the 32-centroid chunks (a ballot over 32 chunks at a time), and runs test1 in
+// dot-product form for every pair of a chunk in reach (lane = fiber, the chunk's 32 screen rows
+// read as broadcasts). The pairs that pass join a short per-warp list, column by column, and
+// every 32 of them are one round of test2 (centre and end points, both orientations) with one
+// pair per lane; the pairs that pass test2 join a second list, and every 32 of those are one
+// round of test3 and test4 (Section 2.3). So the lanes of a round do the same stage of the
+// test, whatever the chunk and column their pairs came from. Each fiber's packed key lives in
+// shared memory (atomicMin; its high word is the fiber's best value, the bound of every later
+// test), so there is no sorted copy, no record list and no overflow path. Groups come from a
+// work counter.
 constexpr int FZ_WARPS = 4;
 constexpr int FZ_CTAS = 5;         // resident CTAs per SM (96 registers a thread)
 constexpr int FZ_STRIDE = NC + 2;  // 65 floats per fiber row in shared memory (odd)
 
 constexpr int FZ_QLEN = 64;  // queued pairs per warp: fewer than 32 wait, plus one round
+constexpr int FZ_ALEN = 64;  // test1 survivors per warp: fewer than 32 wait, plus a column
 constexpr int FZ_MAX_M = 1 << 25;  // a queued pair packs the centroid index in 25 bits
 
-// 9,856 bytes a warp: five 4-warp CTAs an SM (with the 80 registers a thread that six would
+// 10,112 bytes a warp: five 4-warp CTAs an SM (with the 80 registers a thread that six would
 // leave, and test1's rows read through L1, the kernel is slower).
 struct FzWarp {
     float f[32 * FZ_STRIDE];   // the group's fiber rows (column 63: the fiber's length, for TN)
@@ -1120,6 +1123,7 @@ struct FzWarp {
     unsigned long long key[32];  // packed keys; the high word is the fiber's best value so far
     float2 qm[FZ_QLEN];        // queued pairs: partial maxima after test2 (direct, reversed)
     unsigned qe[FZ_QLEN];      //   fiber | live direct << 5 | live reversed << 6 | centroid << 7
+    unsigned al[FZ_ALEN];      // pairs that passed test1, waiting for test2: fiber | centroid << 5
 };
 
 // A fiber's best key value so far (the float bits in its key's high word; all ones when none).
@@ -1214,6 +1218,40 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         const long long f0 = grp * 32;
         const int rows_in = (int)max(0LL, min(32LL, n - f0));
         int qn = 0;  // queued pairs (warp-uniform)
+        int na = 0;  // listed test1 survivors (warp-uniform)
+        // one round of test2 (centre and end points) on 32 listed pairs (`valid`: this lane's
+        // entry is one); the pairs that pass join the queue, and each full 32 of the queue is
+        // one round of test3/test4
+        auto test2_round = [&](unsigned ent, bool valid) {
+            const int fl = (int)(ent & 31u), j = (int)(ent >> 5);
+            const float4* r = g.end_sp + 3 * (size_t)j;
+            const float4 q10 = __ldg(r + 1);  // w: theta^2
+            const float4 q0 = __ldg(r), q20 = __ldg(r + 2);
+            const float* a = S.f + fl * FZ_STRIDE;
+            const float3 p0 = make_float3(a[0], a[1], a[2]);
+            const float3 p10 = make_float3(a[3 * CENTRE], a[3 * CENTRE + 1], a[3 * CENTRE + 2]);
+            const float3 p20 = make_float3(a[3 * (NPTS - 1)], a[3 * (NPTS - 1) + 1],
+                                           a[3 * (NPTS - 1) + 2]);
+            unsigned live = 0u;
+            float md = 0.0f, mr = 0.0f;
+            if (valid)
+                live = fz_phase_a(p0, p10, p20, q0, q10, q20,
+                                  pair_bound2(at, q10.w, key_bound2(fz_best(S, fl), at.cls)),
+                                  at.cls, md, mr, npd);
+            const unsigned bal = __ballot_sync(0xffffffffu, live != 0u);
+            if (live) {
+                const int e = qn + __popc(bal & ((1u << lane) - 1u));
+                S.qm[e] = make_float2(md, mr);
+                S.qe[e] = (unsigned)fl | (live << 5) | ((unsigned)j << 7);
+            }
+            qn += __popc(bal);
+            __syncwarp();
+            if (qn >= 32) {  // one coherent round of test3/test4: the newest 32
+                qn -= 32;
+                fz_phase_b<EXT>(S, qn + lane, at, g, perm, f0, npd);
+                __syncwarp();
+            }
+        };
         // 1. the group's rows (all copies in flight together)
         const unsigned my_src = lane < rows_in ? __ldg(perm + f0 + lane) : 0u;
         __syncwarp();
@@ -1289,79 +1327,30 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                 __syncwarp();
                 if (!__any_sync(0xffffffffu, m != 0u)) continue;
                 surv += __popc(m);
-                unsigned cm = 0u;  // lane b: the fibers whose centroid b passed test1
-#pragma unroll
-                for (int bb = 0; bb < 32; ++bb) {
-                    const unsigned v = __ballot_sync(0xffffffffu, (m >> bb) & 1u);
-                    if (lane == bb) cm = v;
-                }
-                unsigned pre = __popc(cm);
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const unsigned v = __shfl_up_sync(0xffffffffu, pre, off);
-                    if (lane >= off) pre += v;
-                }
-                const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
-                // a round's pair P (column-major): its centroid column bc (the columns whose
-                // prefix is <= P) and fiber fl (the (k+1)-th set bit of that column's mask);
-                // the next round's is located while this round's loads are in flight
-                auto locate = [&](unsigned Pq, int& bc_o, int& fl_o) {
-                    int bc = 0;
-#pragma unroll
-                    for (int step = 16; step; step >>= 1)
-                        if (__shfl_sync(0xffffffffu, pre, bc + step - 1) <= Pq) bc += step;
-                    const unsigned cmb = __shfl_sync(0xffffffffu, cm, bc);
-                    const unsigned below = __shfl_sync(0xffffffffu, pre, bc > 0 ? bc - 1 : 0);
-                    const unsigned kk = Pq - (bc > 0 ? below : 0u);
-                    int fl = 0;
-#pragma unroll
-                    for (int step = 16; step; step >>= 1)  // fl + step <= 31
-                        if ((unsigned)__popc(cmb & ((1u << (fl + step)) - 1u)) <= kk) fl += step;
-                    bc_o = bc;
-                    fl_o = fl;
-                };
-                int bc, fl;
-                locate((unsigned)lane, bc, fl);
-                for (unsigned t0 = 0; t0 < total; t0 += 32) {
-                    const unsigned P = t0 + (unsigned)lane;
-                    // loads for every lane (a lane past the total reads a valid row unused)
-                    const int j = min(32 * cc + bc, at.M - 1);
-                    const float4* r = g.end_sp + 3 * (size_t)j;
-                    const float4 q10 = __ldg(r + 1);  // w: theta^2
-                    const float4 q0 = __ldg(r), q20 = __ldg(r + 2);
-                    const float* a = S.f + fl * FZ_STRIDE;
-                    const float3 p0 = make_float3(a[0], a[1], a[2]);
-                    const float3 p10 = make_float3(a[3 * CENTRE], a[3 * CENTRE + 1],
-                                                   a[3 * CENTRE + 2]);
-                    const float3 p20 = make_float3(a[3 * (NPTS - 1)], a[3 * (NPTS - 1) + 1],
-                                                   a[3 * (NPTS - 1) + 2]);
-                    const float bestv = fz_best(S, fl);
-                    int nbc = 0, nfl = 0;
-                    if (t0 + 32 < total) locate(P + 32, nbc, nfl);
-                    unsigned live = 0u;
-                    float md = 0.0f, mr = 0.0f;
-                    if (P < total)
-                        live = fz_phase_a(p0, p10, p20, q0, q10, q20,
-                                          pair_bound2(at, q10.w, key_bound2(bestv, at.cls)),
-                                          at.cls, md, mr, npd);
-                    const unsigned bal = __ballot_sync(0xffffffffu, live != 0u);
-                    if (live) {
-                        const int e = qn + __popc(bal & ((1u << lane) - 1u));
-                        S.qm[e] = make_float2(md, mr);
-                        S.qe[e] = (unsigned)fl | (live << 5) | ((unsigned)j << 7);
-                    }
-                    qn += __popc(bal);
-                    __syncwarp();
-                    if (qn >= 32) {  // one coherent round of test3/test4: the newest 32
-                        qn -= 32;
-                        fz_phase_b<EXT>(S, qn + lane, at, g, perm, f0, npd);
+                // the chunk's survivors join the warp's list column by column (a ballot per
+                // column that any fiber passed); each full 32 is one round of test2
+                unsigned cols = __reduce_or_sync(0xffffffffu, m);
+                while (cols) {
+                    const int b = __ffs(cols) - 1;
+                    cols &= cols - 1;
+                    const unsigned v = __ballot_sync(0xffffffffu, (m >> b) & 1u);
+                    if ((m >> b) & 1u)
+                        S.al[na + __popc(v & ((1u << lane) - 1u))] =
+                            (unsigned)lane | ((unsigned)(32 * cc + b) << 5);
+                    na += __popc(v);
+                    if (na >= 32) {
                         __syncwarp();
+                        na -= 32;
+                        test2_round(S.al[na + lane], true);
                     }
-                    bc = nbc;
-                    fl = nfl;
                 }
                 __syncwarp();
             }
+        }
+        if (na > 0) {  // the group's last test1 survivors
+            __syncwarp();
+            test2_round(S.al[lane < na ? lane : 0], lane < na);
+            na = 0;
         }
         if (qn > 0) {  // the group's last queued pairs
             if (lane < qn) fz_phase_b<EXT>(S, lane, at, g, perm, f0, npd);
