@@ -1115,7 +1115,7 @@ constexpr int FZ_QLEN = 64;  // queued pairs per warp: fewer than 32 wait, plus 
 constexpr int FZ_ALEN = 64;  // test1 survivors per warp: fewer than 32 wait, plus a column
 constexpr int FZ_MAX_M = 1 << 25;  // a queued pair packs the centroid index in 25 bits
 
-// 10,112 bytes a warp: five 4-warp CTAs an SM (with the 80 registers a thread that six would
+// 10,144 bytes a warp: five 4-warp CTAs an SM (with the 80 registers a thread that six would
 // leave, and test1's rows read through L1, the kernel is slower).
 struct FzWarp {
     float f[32 * FZ_STRIDE];   // the group's fiber rows (column 63: the fiber's length, for TN)
@@ -1124,6 +1124,7 @@ struct FzWarp {
     float2 qm[FZ_QLEN];        // queued pairs: partial maxima after test2 (direct, reversed)
     unsigned qe[FZ_QLEN];      //   fiber | live direct << 5 | live reversed << 6 | centroid << 7
     unsigned al[FZ_ALEN];      // pairs that passed test1, waiting for test2: fiber | centroid << 5
+    float box[8];              // the group's centre-point box (lo xyz, hi xyz)
 };
 
 // A fiber's best key value so far (the float bits in its key's high word; all ones when none).
@@ -1207,7 +1208,6 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     FzWarp& S = reinterpret_cast<FzWarp*>(fz_smem)[w];
-    unsigned long long screened = 0, surv = 0;
     unsigned npd = 0;
     // groups taken from a counter (their costs vary with the density of the atlas around
     // them; a fixed stride left a long tail), the next one fetched while this one finishes
@@ -1278,8 +1278,7 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         }
         S.key[lane] = finite ? ~0ull : NAN_KEY;
         S.f[lane * FZ_STRIDE + NC] = at.cls != CLS_EQ2 && finite ? poly_length(a) : 0.0f;
-        UnitBox box;
-        {
+        {   // (kept in shared memory: it is read once per 32 chunks)
             float lo[3], hi[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -1292,12 +1291,19 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                     hi[r] = fmaxf(hi[r], __shfl_xor_sync(0xffffffffu, hi[r], off));
                 }
             }
-            box = UnitBox{lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                if (lane == r) S.box[r] = lo[r];
+                if (lane == r + 3) S.box[r + 3] = hi[r];
+            }
         }
         __syncwarp();
+        unsigned surv = 0, blocks = 0;  // this group's test1 survivors (lane), chunks tested
         // 3. the chunks in reach
-        for (int k0 = 0; box.lx <= box.hx && k0 < n_chunks; k0 += 32) {
+        const bool any_finite = S.box[0] <= S.box[3];
+        for (int k0 = 0; any_finite && k0 < n_chunks; k0 += 32) {
             const int cq = k0 + lane;
+            const UnitBox box{S.box[0], S.box[1], S.box[2], S.box[3], S.box[4], S.box[5]};
             unsigned act = __ballot_sync(0xffffffffu, cq < n_chunks && block_active(box, tbox, cq));
             while (act) {
                 const int cc = k0 + __ffs(act) - 1;
@@ -1323,7 +1329,7 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
                     const float t = fmaf(z, q.z, fmaf(y, q.y, fmaf(x, q.x, q.w)));
                     m |= (t >= he ? 1u : 0u) << i;
                 }
-                screened += 32;
+                ++blocks;
                 __syncwarp();
                 if (!__any_sync(0xffffffffu, m != 0u)) continue;
                 surv += __popc(m);
@@ -1358,7 +1364,13 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         }
         __syncwarp();
         long long next = 0;
-        if (lane == 0) next = (long long)atomicAdd(g.cnt + 4, 1ull);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+        if (lane == 0) {
+            next = (long long)atomicAdd(g.cnt + 4, 1ull);
+            if (surv) atomicAdd(g.cnt + 2, (unsigned long long)surv);
+            if (blocks) atomicAdd(g.cnt + 3, 1024ull * blocks);
+        }
         // 4. results in the caller's order
         if (lane < rows_in) {
             const unsigned long long k = S.key[lane];
@@ -1393,16 +1405,8 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
     }
     unsigned long long tot = npd;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        tot += __shfl_down_sync(0xffffffffu, tot, off);
-        screened += __shfl_down_sync(0xffffffffu, screened, off);
-        surv += __shfl_down_sync(0xffffffffu, surv, off);
-    }
-    if (lane == 0) {
-        if (surv) atomicAdd(g.cnt + 2, surv);
-        if (screened) atomicAdd(g.cnt + 3, screened);
-        if (tot) atomicAdd(g.cnt + 5, tot);
-    }
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, off);
+    if (lane == 0 && tot) atomicAdd(g.cnt + 5, tot);
 }
 
 __global__ void k_gemm_stats(const unsigned long long* __restrict__ cnt, long long pairs,
