@@ -587,7 +587,7 @@ def run_batch(args, world, rank, dev, dist):
     at = binding.Atlas(torch.as_tensor(atlas_np.centroids, device=dev),
                        torch.as_tensor(atlas_np.bundle_of, device=dev),
                        torch.as_tensor(atlas_np.thresholds, device=dev))
-    mode = "plain" if args.mode == "best" else args.mode
+    mode = "culled_fused" if args.mode == "best" else args.mode
     tune.tune(at, fibs[0], mode)
     labs = [torch.empty(f.shape[0], dtype=torch.int32, device=dev) for f in fibs]
     dsts = [torch.empty(f.shape[0], device=dev) for f in fibs]
@@ -631,7 +631,7 @@ def run_streamlines(args, world, rank, dev, dist):
     at = binding.Atlas(torch.as_tensor(atlas_np.centroids, device=dev),
                        torch.as_tensor(atlas_np.bundle_of, device=dev),
                        torch.as_tensor(atlas_np.thresholds, device=dev))
-    mode = "plain_culled" if args.mode == "best" else args.mode
+    mode = "culled_fused" if args.mode == "best" else args.mode
     stream = torch.cuda.current_stream(dev)
     out = torch.empty((n, 21, 3), device=dev)
     ms_rs = cuda_time(lambda: binding.seg_resample(pts, off, out=out, stream=stream), args.steps,
@@ -738,7 +738,7 @@ def run_extras(dev, stream, atlas_np, fib_np, labels_head, dist_head, head_mode)
     dsts = [torch.empty(f.shape[0], device=dev) for f in fibs]
     total = sum(int(f.shape[0]) for f in fibs)
     out["batch16"] = {"subjects": 16, "fibers": total, "modes": {}}
-    for m in ("plain_culled", "gemm_bf16", "plain"):
+    for m in ("culled_fused", "plain_culled", "gemm_bf16", "plain"):
         ms = cuda_time(lambda: binding.seg_label_batch(atb, fibs, m, labs, dsts, stream=stream),
                        3 if m == "plain" else 5, stream)
         out["batch16"]["modes"][m] = {"ms_per_batch": ms, "fibers_per_s": total / (ms / 1e3)}
@@ -753,7 +753,7 @@ def run_extras(dev, stream, atlas_np, fib_np, labels_head, dist_head, head_mode)
     lw = torch.empty(xw.shape[0], dtype=torch.int32, device=dev)
     out["whole_brain"] = {"workload": "subject4145k_atlas44k", "fibers": int(xw.shape[0]),
                           "centroids": aw.M, "modes": {}}
-    for m in ("plain_culled", "gemm_bf16"):
+    for m in ("culled_fused", "plain_culled", "gemm_bf16"):
         ms = cuda_time(lambda: binding.seg_label(atw, xw, m, lw, stream=stream), 3, stream)
         out["whole_brain"]["modes"][m] = {"ms_per_step": ms,
                                          "fibers_per_s": xw.shape[0] / (ms / 1e3)}
