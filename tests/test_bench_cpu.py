@@ -17,6 +17,7 @@ def test_traffic_only_for_the_captured_instantiation_and_size():
     assert bench.traffic_for("k_exact_blocks", "gemm_bf16", n) == t["k_exact_blocks@gemm_bf16"]
     assert bench.traffic_for("k_gemm_screen", "gemm_bf16", n) == t["k_gemm_screen@gemm_bf16"]
     assert bench.traffic_for("k_label_plain", "plain", n) == t["k_label_plain"]
+    assert bench.traffic_for("k_fused", "culled_fused", n) == t["k_fused@culled_fused"]
     # other template instantiations and other sizes were not captured
     assert bench.traffic_for("k_gemm_screen", "gemm_inv_tf32", n) is None
     assert bench.traffic_for("k_exact_blocks", "gemm_tf32", n) is None
