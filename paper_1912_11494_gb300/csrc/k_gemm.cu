@@ -332,8 +332,11 @@ k_prep_a(FiberSrc fsrc, const unsigned* __restrict__ perm, long long n,
     const int rows_in = (int)max(0LL, min(32LL, n - r0));
     float* si = reinterpret_cast<float*>(s_buf[w]);
     const unsigned src_row = lane < rows_in ? __ldg(perm + r0 + lane) : 0u;
+    // each lane finds its own row (for several subjects, a search of the work table), then
+    // the warp copies the rows one after another
+    const float* my_row = fsrc.row(src_row);
     for (int r = 0; r < rows_in; ++r) {  // all 63 x 32 copies in flight at once
-        const float* src = fsrc.row(__shfl_sync(0xffffffffu, src_row, r));
+        const float* src = shfl_ptr(my_row, r);
         cp_async4(si + r * PREP_STRIDE + lane, src + lane);
         if (lane < NC - 32) cp_async4(si + r * PREP_STRIDE + 32 + lane, src + 32 + lane);
     }
@@ -1254,9 +1257,10 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         };
         // 1. the group's rows (all copies in flight together)
         const unsigned my_src = lane < rows_in ? __ldg(perm + f0 + lane) : 0u;
+        const float* my_row = src.row(my_src);  // (a work-table search per lane, not per row)
         __syncwarp();
         for (int r = 0; r < rows_in; ++r) {
-            const float* p = src.row(__shfl_sync(0xffffffffu, my_src, r));
+            const float* p = shfl_ptr(my_row, r);
             cp_async4(S.f + r * FZ_STRIDE + lane, p + lane);
             if (lane < NC - 32) cp_async4(S.f + r * FZ_STRIDE + 32 + lane, p + 32 + lane);
         }

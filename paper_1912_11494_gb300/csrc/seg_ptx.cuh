@@ -85,6 +85,15 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Lane `src`'s pointer, for the whole warp.
+template <class T>
+__device__ __forceinline__ T* shfl_ptr(T* p, int src) {
+    const unsigned long long v = reinterpret_cast<unsigned long long>(p);
+    const unsigned lo = __shfl_sync(0xffffffffu, (unsigned)v, src);
+    const unsigned hi = __shfl_sync(0xffffffffu, (unsigned)(v >> 32), src);
+    return reinterpret_cast<T*>(((unsigned long long)hi << 32) | lo);
+}
+
 // cp.async (LDGSTS): global -> shared without registers; wait_all waits for this thread's.
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
