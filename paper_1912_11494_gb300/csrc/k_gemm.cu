@@ -335,6 +335,7 @@ k_prep_a(FiberSrc fsrc, const unsigned* __restrict__ perm, long long n,
     // each lane finds its own row (for several subjects, a search of the work table), then
     // the warp copies the rows one after another
     const float* my_row = fsrc.row(src_row);
+#pragma unroll 4
     for (int r = 0; r < rows_in; ++r) {  // all 63 x 32 copies in flight at once
         const float* src = shfl_ptr(my_row, r);
         cp_async4(si + r * PREP_STRIDE + lane, src + lane);
@@ -1259,6 +1260,7 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         const unsigned my_src = lane < rows_in ? __ldg(perm + f0 + lane) : 0u;
         const float* my_row = src.row(my_src);  // (a work-table search per lane, not per row)
         __syncwarp();
+#pragma unroll 4
         for (int r = 0; r < rows_in; ++r) {
             const float* p = shfl_ptr(my_row, r);
             cp_async4(S.f + r * FZ_STRIDE + lane, p + lane);
@@ -1269,9 +1271,10 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         // 2. this lane's fiber: screen values, key, length; the group's centre-point box
         const float* a = S.f + lane * FZ_STRIDE;
         bool finite = lane < rows_in;  // every centred coordinate finite, as in the other modes
-        for (int k = 0; k < NC && finite; k += 3)
-            finite = isfinite(a[k] - at.c0x) && isfinite(a[k + 1] - at.c0y) &&
-                     isfinite(a[k + 2] - at.c0z);
+#pragma unroll
+        for (int k = 0; k < NC; k += 3)
+            finite &= isfinite(a[k] - at.c0x) & isfinite(a[k + 1] - at.c0y) &
+                      isfinite(a[k + 2] - at.c0z);
         float x = 0.f, y = 0.f, z = 0.f, h = NAN;  // NaN never passes test1
         if (finite) {
             x = a[3 * CENTRE] - at.c0x;
@@ -1287,13 +1290,8 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const float c = finite ? a[3 * CENTRE + r] : 0.0f;
-                lo[r] = finite ? c : INFINITY;
-                hi[r] = finite ? c : -INFINITY;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    lo[r] = fminf(lo[r], __shfl_xor_sync(0xffffffffu, lo[r], off));
-                    hi[r] = fmaxf(hi[r], __shfl_xor_sync(0xffffffffu, hi[r], off));
-                }
+                lo[r] = warp_min(finite ? c : INFINITY);
+                hi[r] = warp_max(finite ? c : -INFINITY);
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -1368,8 +1366,7 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         }
         __syncwarp();
         long long next = 0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+        surv = __reduce_add_sync(0xffffffffu, surv);
         if (lane == 0) {
             next = (long long)atomicAdd(g.cnt + 4, 1ull);
             if (surv) atomicAdd(g.cnt + 2, (unsigned long long)surv);
