@@ -297,7 +297,7 @@ LAUNCH_SLOTS = ("plain", "gemm_sort", "gemm_prep", "gemm_screen", "cull_screen",
 # the finalize scope the overflow rescan and the label write)
 KERNELS_PER_SLOT = {"plain": 1, "gemm_sort": 4, "gemm_prep": 3, "gemm_screen": 1,
                     "cull_screen": 1, "gemm_exact": 1, "gemm_finalize": 2,
-                    "culled_fused": 3}
+                    "culled_fused": 2}
 
 
 def kernels_per_slot(mode: str, slot: str) -> int:

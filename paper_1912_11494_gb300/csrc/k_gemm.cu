@@ -546,6 +546,25 @@ __global__ void k_tile_box(const float4* __restrict__ ctr_sp, int M, int per, in
     tbox[2 * t + 1] = hi;
 }
 
+// Boxes of windows of 32 consecutive chunk boxes (lo.w the largest theta^2, hi.w the smallest):
+// a unit out of a window's reach is out of reach of each of its chunks.
+__global__ void k_window_box(const float4* __restrict__ tbox, int n_chunks, int n_windows,
+                             float4* __restrict__ wbox) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_windows) return;
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, -INFINITY);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, INFINITY);
+    for (int c = 32 * t; c < min(n_chunks, 32 * (t + 1)); ++c) {
+        const float4 a = tbox[2 * c], b = tbox[2 * c + 1];
+        lo.x = fminf(lo.x, a.x), lo.y = fminf(lo.y, a.y), lo.z = fminf(lo.z, a.z);
+        hi.x = fmaxf(hi.x, b.x), hi.y = fmaxf(hi.y, b.y), hi.z = fmaxf(hi.z, b.z);
+        lo.w = fmaxf(lo.w, a.w);
+        hi.w = fminf(hi.w, b.w);
+    }
+    wbox[2 * t] = lo;
+    wbox[2 * t + 1] = hi;
+}
+
 // Spatial-order copies of the atlas for the GEMM modes (centroid rows point-major: point i as
 // the float4 (x, y, z, 0), CROW4 per row).
 __global__ void k_prep_spatial(AtlasView at, const int* __restrict__ sp_s, float4* cen_sp,
@@ -1202,8 +1221,8 @@ template <bool EXT>
 __global__ void __launch_bounds__(FZ_WARPS * 32, FZ_CTAS)
 k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long n_groups,
         AtlasView at_in, GemmScratch g, const float4* __restrict__ scr_sp,
-        const float4* __restrict__ tbox, int n_chunks, int* labels, float* dist, int* cidx,
-        unsigned char* orient) {
+        const float4* __restrict__ tbox, const float4* __restrict__ wbox, int n_chunks,
+        int* labels, float* dist, int* cidx, unsigned char* orient) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     AtlasView at = at_in;
     if (!EXT) {
@@ -1306,6 +1325,7 @@ k_fused(FiberSrc src, const unsigned* __restrict__ perm, long long n, long long 
         for (int k0 = 0; any_finite && k0 < n_chunks; k0 += 32) {
             const int cq = k0 + lane;
             const UnitBox box{S.box[0], S.box[1], S.box[2], S.box[3], S.box[4], S.box[5]};
+            if (!block_active(box, wbox, k0 / 32)) continue;  // the whole window out of reach
             unsigned act = __ballot_sync(0xffffffffu, cq < n_chunks && block_active(box, tbox, cq));
             while (act) {
                 const int cc = k0 + __ffs(act) - 1;
@@ -1886,6 +1906,14 @@ seg_status prep_gemm_atlas(const AtlasView& at, const int* sp_host, int max_per_
     k_prep_b_inv<<<bi, threads, 0, st>>>(at, g->sp_s, 1, g->cols_inv, g->cols_inv_pad, g->bi_bf16);
     k_prep_b_inv<<<bi, threads, 0, st>>>(at, g->sp_s, 2, g->cols_inv, g->cols_inv_pad, g->bi_tf32);
     if ((e = cudaGetLastError())) return cuda_fail(e, "gemm operand prep");
+    // the fused mode's chunk boxes (orientation-free chunks of 32 centroids) and window boxes
+    const int nc = g->cols_inv_pad / 32, nw = (nc + 31) / 32;
+    if ((e = cudaMalloc(&g->tbox32, (size_t)nc * 2 * sizeof(float4))) ||
+        (e = cudaMalloc(&g->wbox32, (size_t)nw * 2 * sizeof(float4))))
+        return cuda_fail(e, "gemm chunk boxes");
+    k_tile_box<<<(nc + 127) / 128, 128, 0, st>>>(g->ctr_sp, at.M, 32, nc, g->tbox32);
+    k_window_box<<<(nw + 127) / 128, 128, 0, st>>>(g->tbox32, nc, nw, g->wbox32);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "gemm chunk boxes");
     return SEG_OK;
 }
 
@@ -1900,6 +1928,8 @@ void free_gemm_atlas(GemmAtlas* g) {
     cudaFree(g->ctr_sp);
     cudaFree(g->scr_sp);
     cudaFree(g->end_sp);
+    cudaFree(g->tbox32);
+    cudaFree(g->wbox32);
     cudaFree(g->stats);
     *g = GemmAtlas{};
 }
@@ -2047,8 +2077,6 @@ cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, 
     }
     if (!e && c.fused) {
         ProfScope ps(prof, PROF_FUSED, st);
-        k_tile_box<<<(c.n_chunks + 127) / 128, 128, 0, st>>>(ga->ctr_sp, at.M, 32, c.n_chunks,
-                                                            c.tbox);
         const long long n_groups = (n + 31) / 32;
         const bool ext = at.cls != CLS_EQ2 || at.multi != nullptr;
         auto kern = ext ? k_fused<true> : k_fused<false>;
@@ -2059,8 +2087,8 @@ cudaError_t gemm_enqueue(const GemmCall& c, const AtlasView& at, GemmAtlas* ga, 
         kern<<<(unsigned)std::min<long long>((n_groups + FZ_WARPS - 1) / FZ_WARPS,
                                              (long long)sms * FZ_CTAS),
                FZ_WARPS * 32, FZ_WARPS * sizeof(FzWarp), st>>>(
-            src, c.perm, n, n_groups, at, g, ga->scr_sp, c.tbox, c.n_chunks, labels, dist, cidx,
-            orient);
+            src, c.perm, n, n_groups, at, g, ga->scr_sp, ga->tbox32, ga->wbox32, c.n_chunks,
+            labels, dist, cidx, orient);
         if (!dbg_bits) k_gemm_stats<<<1, 1, 0, st>>>(g.cnt, n * (long long)c.cols, ga->stats);
         return cudaGetLastError();
     }

@@ -74,6 +74,9 @@ struct GemmAtlas {
     float4* ctr_sp = nullptr; // [M] centre point and theta^2 in spatial order
     float4* scr_sp = nullptr; // [M rounded up to 32] the test1 screen row (AtlasView::scr2) in
                               // spatial order; the pad (0, 0, 0, -inf) passes no fiber
+    float4* tbox32 = nullptr; // [cols_inv_pad / 32][2] boxes of the 32-centroid chunks (lo, hi;
+                              // lo.w the largest theta^2, hi.w the smallest)
+    float4* wbox32 = nullptr; // [ceil(chunks / 32)][2] boxes of 32 consecutive chunks
     float4* end_sp = nullptr; // [M][3] points 0, 10, 20 in spatial order (w: the length,
                               // theta^2, 0): what test1 and test2 read, 48 bytes a centroid
     long long* stats = nullptr;  // [5] pairs, survivors, overflow fibers, screened pairs,
