@@ -1166,6 +1166,25 @@ __device__ __forceinline__ float pd2q(float3 p, float4 q) {
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
+// test3 and test4 stages (as mid4 / rest17) in an orientation o chosen per lane: fiber point i
+// pairs with centroid point i (o = 0) or 20 - i (o = 1).
+__device__ __forceinline__ float fz_mid4(const float* a, const float4* b, float m, int o) {
+    constexpr int L = NPTS - 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = test3_point(q);
+        m = fmaxf(m, pd2v(a, i, b, o ? L - i : i));
+    }
+    return m;
+}
+__device__ __forceinline__ float fz_rest17(const float* a, const float4* b, float m, int o) {
+    constexpr int L = NPTS - 1;
+#pragma unroll
+    for (int i = 1; i < L; ++i)
+        if (!is_early_point(i)) m = fmaxf(m, pd2v(a, i, b, o ? L - i : i));
+    return m;
+}
+
 // p0, p10, p20: the fiber's points 0, 10, 20; q0, q10, q20: the centroid's.
 __device__ __forceinline__ unsigned fz_phase_a(float3 p0, float3 p10, float3 p20, float4 q0,
                                                float4 q10, float4 q20, float bound, int cls,
@@ -1202,10 +1221,27 @@ __device__ __forceinline__ void fz_phase_b(FzWarp& S, int e, const AtlasView& at
     float md = mm.x, mr = mm.y;
     bool ad = ((fl_bits >> 5) & 1u) && md <= bound;
     bool ar = ((fl_bits >> 6) & 1u) && mr <= bound;
-    if (ad) { md = mid4<0>(a, b, md); ad = md <= bound; npd += 4; }
-    if (ar) { mr = mid4<1>(a, b, mr); ar = mr <= bound; npd += 4; }
-    if (ad) { md = rest17<0>(a, b, md); ad = md <= bound; npd += 14; }
-    if (ar) { mr = rest17<1>(a, b, mr); ar = mr <= bound; npd += 14; }
+    // Each lane's first live orientation runs in one code path for the whole warp (the
+    // centroid point it pairs with is picked per lane), so a round whose pairs differ in
+    // orientation does not run twice; the reversed one runs again only where both are live.
+    const int o = ad ? 0 : 1;
+    float m = ad ? md : mr;
+    bool live = ad || ar;
+    bool live2 = ad && ar;
+    float m2 = mr;
+    if (live) { m = fz_mid4(a, b, m, o); live = m <= bound; npd += 4; }
+    if (live2) { m2 = fz_mid4(a, b, m2, 1); live2 = m2 <= bound; npd += 4; }
+    if (live) { m = fz_rest17(a, b, m, o); live = m <= bound; npd += 14; }
+    if (live2) { m2 = fz_rest17(a, b, m2, 1); live2 = m2 <= bound; npd += 14; }
+    if (o == 0) {
+        md = m;
+        ad = live;
+        mr = m2;
+        ar = live2;
+    } else {
+        mr = m;
+        ar = live;
+    }
     if (!(ad || ar)) return;
     const bool dir = ad && (!ar || md <= mr);
     const float d2 = dir ? md : mr;
