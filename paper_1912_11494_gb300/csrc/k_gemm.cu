@@ -1120,7 +1120,8 @@ __device__ __forceinline__ float rest17(const float* a, const float4* b, float m
 // One warp owns a 32-fiber group of the locality order from start to finish: it gathers the
 // group's 32 rows from the caller's array into shared memory once (odd row stride, so lanes
 // reading different rows at one column never share a bank), tests the group's centre-point box
-// against the 32-centroid chunks (a ballot over 32 chunks at a time), and runs test1 in
+// against the 32-centroid chunks (a window of 32 chunks out of reach is skipped whole, the
+// others take a ballot over their 32 chunks), and runs test1 in
 // dot-product form for every pair of a chunk in reach (lane = fiber, the chunk's 32 screen rows
 // read as broadcasts). The pairs that pass join a short per-warp list, column by column, and
 // every 32 of them are one round of test2 (centre and end points, both orientations) with one
@@ -1205,8 +1206,8 @@ __device__ __forceinline__ unsigned fz_phase_a(float3 p0, float3 p10, float3 p20
 }
 
 // Phase B of a queued pair: test3 and test4 in its live orientations against min(theta^2, the
-// fiber's best so far), then the merge into the fiber's key and best (Algorithm 1's tie rule:
-// exits are strict, so equal values still reach the atomicMin of the packed key).
+// fiber's best so far), then the merge into the fiber's packed key (Algorithm 1's tie rule:
+// exits are strict, so equal values still reach the atomicMin of the key).
 template <bool EXT>
 __device__ __forceinline__ void fz_phase_b(FzWarp& S, int e, const AtlasView& at,
                                            const GemmScratch& g, const unsigned* perm,
