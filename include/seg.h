@@ -80,8 +80,8 @@ typedef enum {
      * block culling (32-fiber groups x 32-centroid chunks), then test1 (the centre point,
      * Section 2.3) on CUDA cores for every pair of the remaining blocks, then the same exact
      * test (both orientations) on the pairs that pass. Labels and distances equal
-     * SEG_MODE_PLAIN's. The culling is not in the paper (its Section 2.4 "data locality" is a
-     * cache argument); it is reported as its own algorithmic mode. */
+     * SEG_MODE_PLAIN's. The culling is not in the paper (its Section 2.4 data-locality argument
+     * is about caches); it is reported as its own algorithmic mode. */
     SEG_MODE_PLAIN_CULLED = 5,
     /* SEG_MODE_PLAIN_CULLED's work in one kernel after the locality sort: a warp takes a
      * 32-fiber group, stages its rows once, culls the 32-centroid chunks by centre-point box,
@@ -155,9 +155,9 @@ seg_status seg_label(const seg_atlas* atlas, const float* d_fibers, int64_t n, s
                      void* stream);
 
 /*
- * Every bundle each fiber passes, besides the closest one (Section 2.4, "Classification of
- * fibers": the paper's original algorithm could assign a fiber to several bundles; the new one
- * keeps the closest). d_bundle_bits is device uint32 [n][words_per_fiber], overwritten: bit b
+ * Every bundle each fiber passes, besides the closest one (Section 2.4, on classifying fibers:
+ * the paper's earlier algorithm could give a fiber several bundles; its new one keeps the
+ * closest). d_bundle_bits is device uint32 [n][words_per_fiber], overwritten: bit b
  * of fiber f's row (word b / 32, bit b % 32) is set when some centroid of bundle b passes its
  * threshold for f under the atlas's classification (d_ME <= theta, or D <= theta with TN).
  * words_per_fiber >= ceil(B / 32). d_labels (required) and d_dist (or NULL) receive seg_label's
@@ -186,8 +186,8 @@ seg_status seg_label_host(const seg_atlas* atlas, const float* h_fibers, int64_t
 
 /*
  * Resample raw streamlines to the 21 arc-length-equidistant points the labelling takes
- * (Section 2.3: subject fibers are resampled using 21 equidistant points; the paper's
- * tractography steps 0.2 mm, Section 2.1). Not tied to an atlas.
+ * (Section 2.3 works on fibers of 21 equidistant points; the paper's tractography steps
+ * 0.2 mm, Section 2.1). Not tied to an atlas.
  *   d_points  device float32 [P][3]: the points of every streamline, one streamline after
  *             another (4-byte aligned).
  *   d_offsets device int64 [n + 1] (8-byte aligned): streamline f has the points

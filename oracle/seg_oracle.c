@@ -20,8 +20,7 @@
  *
  * Two labelling modes give identical results by construction:
  *   brute   - all 42 point distances of every pair, then the rule above (the plain definition);
- *   cascade - the paper's progressive discarding (Section 2.3, "Progressive fiber discarding",
- *             and Algorithm 1): test1 centre point, test2 end points, test3 four intermediate
+ *   cascade - the paper's progressive discarding of fibers (Section 2.3 and Algorithm 1): test1 centre point, test2 end points, test3 four intermediate
  *             points, test4 all points, each orientation stopping at its first point distance
  *             above the threshold (Section 2.4, early evaluation of the discarding criterion).
  *
@@ -660,7 +659,7 @@ int oracle_lengths(const float *fib, int64_t n, double *len) {
 
 /* ---- resampling of raw streamlines (Section 2.3) ----------------------------------------- */
 
-/* "Subject fibers are resampled using 21 equidistant points" (Section 2.3), read as equidistant
+/* Section 2.3 works on subject fibers of 21 equidistant points; read here as equidistant
  * in arc length along the streamline's polyline: with cumulative lengths c_0 = 0 <= c_1 <= ...
  * <= c_(m-1) = L over its m points, output point k (0 <= k <= 20) is the point at arc length
  * s_k = k L / 20, linearly interpolated inside the first segment (j, j+1) with c_j < s_k <=
@@ -707,7 +706,7 @@ int oracle_resample(const float *points, const int64_t *offsets, int64_t n, doub
     return 0;
 }
 
-/* ---- multi-label output (Section 2.4, "Classification of fibers") ------------------------ */
+/* ---- multi-label output (Section 2.4, on classifying fibers) ----------------------------- */
 
 /* Every bundle a fiber passes: bit b of fiber f's row (words uint32 words) is set when some
  * centroid of bundle b passes its threshold under classification cls (0 Eq. 2: d_ME <= theta;

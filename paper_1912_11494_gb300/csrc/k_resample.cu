@@ -1,5 +1,5 @@
-// Resampling of raw streamlines to 21 arc-length-equidistant points (Section 2.3: "subject
-// fibers are resampled using 21 equidistant points"), ahead of the labelling.
+// Resampling of raw streamlines to 21 arc-length-equidistant points (Section 2.3 works on fibers
+// of 21 equidistant points), ahead of the labelling.
 //
 // One warp per streamline (CSR: points [P][3], offsets [n+1]). The lanes read 32 consecutive
 // points at a time (coalesced), each lane measures one segment, and a warp scan gives the

@@ -1,4 +1,4 @@
-"""GPU multi-label output (seg_label_multi; Section 2.4, "Classification of fibers"): every
+"""GPU multi-label output (seg_label_multi; Section 2.4, on classifying fibers): every
 bundle a fiber passes, against the FP64 oracle. Bits are compared wherever the oracle calls
 them decidable (the bundle's best centroid is not within 2e-3 mm of its threshold); the
 closest-bundle labels equal seg_label's bit for bit, and every mode gives identical bits."""
