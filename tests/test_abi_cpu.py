@@ -78,3 +78,19 @@ def test_argument_errors_before_device_work(lib):
     assert lib.seg_apply_affine(ctypes.c_void_p(0x1002), 1, aff, ctypes.c_void_p(0x2000),
                                 None) == 1
     assert b"aligned" in lib.seg_last_error()
+
+
+def test_modes_match_the_header(lib):
+    """binding.MODES names every seg_mode the header declares, with its value; every mode has at
+    least one tile configuration and an unknown mode has none (host-side query)."""
+    text = open(os.path.join(ROOT, "include", "seg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    enum = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"SEG_MODE_(\w+)\s*=\s*(\d+)", text)}
+    assert enum == binding.MODES
+    for name, value in enum.items():
+        n = lib.seg_num_configs(value)
+        assert n >= 1, name
+        if name in ("plain_culled", "culled_fused"):
+            assert n == 1
+    assert lib.seg_num_configs(max(enum.values()) + 1) == 0
